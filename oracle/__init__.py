@@ -1,0 +1,194 @@
+"""Plain CPU oracle for the checkerboard Metropolis sweep (TEST INFRASTRUCTURE).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It wraps ``isg_oracle.c`` (one int8 per
+spin, the paper's definitions written out plainly) through ctypes and shares no
+code with the CUDA library in ``paper_1411_0127_gb300``.
+
+Passages followed (arXiv:1411.0127): Eq. (1) Hamiltonian, Eq. (2) bimodal
+couplings, Sec. 1 checkerboard colours, Sec. 4 Metropolis rule and integer
+threshold comparison, Sec. 3 MINSTD and MT19937.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "isg_oracle.c")
+_HDR = os.path.join(_HERE, "isg_oracle.h")
+_LIB = os.path.join(_HERE, "libisg_oracle.so")
+
+RNG_MINSTD = 0
+RNG_MT19937 = 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (portable flags: same results on x86 and Arm)."""
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
+        return _LIB
+    tmp = _LIB + ".tmp.%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        u64, i64, i32, u32, dbl = (ctypes.c_uint64, ctypes.c_int64, ctypes.c_int,
+                                   ctypes.c_uint32, ctypes.c_double)
+        vp = ctypes.c_void_p
+        sig = {
+            "or_splitmix64": (u64, [u64, u64]),
+            "or_thresholds": (None, [dbl, vp]),
+            "or_rows_per_stream": (i64, [i32]),
+            "or_num_streams": (i64, [i32]),
+            "or_mt19937_outputs": (None, [u32, vp, i64]),
+            "or_minstd_outputs": (None, [u32, vp, i64]),
+            "or_unsatisfied": (i32, [ctypes.c_int8, vp, vp]),
+            "or_accept": (i32, [i32, u32, vp]),
+            "or_create": (vp, [i32, u64, u64, dbl, i32]),
+            "or_destroy": (None, [vp]),
+            "or_sweep": (None, [vp, i64, i32]),
+            "or_energy": (i64, [vp]),
+            "or_tracked_energy": (i64, [vp]),
+            "or_overlap": (i64, [vp, vp]),
+            "or_hash": (u64, [vp]),
+            "or_draws_per_stream_done": (i64, [vp, i64]),
+            "or_get_spins": (None, [vp, vp]),
+            "or_set_spins": (None, [vp, vp]),
+            "or_get_couplings": (None, [vp, vp]),
+            "or_set_couplings": (None, [vp, vp]),
+            "or_move_counts": (None, [vp, vp, vp]),
+            "or_acceptance_trial": (None, [i32, u32, dbl, i64, vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data
+
+
+def splitmix64(seed: int, n: int) -> int:
+    return int(lib().or_splitmix64(seed & (2**64 - 1), n))
+
+
+def thresholds(beta: float) -> np.ndarray:
+    t = np.zeros(4, dtype=np.uint32)
+    lib().or_thresholds(float(beta), _ptr(t))
+    return t
+
+
+def rows_per_stream(L: int) -> int:
+    return int(lib().or_rows_per_stream(L))
+
+
+def num_streams(L: int) -> int:
+    return int(lib().or_num_streams(L))
+
+
+def mt19937_outputs(seed: int, n: int) -> np.ndarray:
+    out = np.empty(n, dtype=np.uint32)
+    lib().or_mt19937_outputs(seed & 0xFFFFFFFF, _ptr(out), n)
+    return out
+
+
+def minstd_outputs(x0: int, n: int) -> np.ndarray:
+    out = np.empty(n, dtype=np.uint32)
+    lib().or_minstd_outputs(x0, _ptr(out), n)
+    return out
+
+
+def unsatisfied(s: int, nb, J) -> int:
+    nb = np.ascontiguousarray(nb, dtype=np.int8)
+    J = np.ascontiguousarray(J, dtype=np.int8)
+    return int(lib().or_unsatisfied(int(s), _ptr(nb), _ptr(J)))
+
+
+def acceptance_trial(kind: int, seed: int, beta: float, n: int) -> np.ndarray:
+    """Accepted counts out of n decisions for u = 0, 1, 2 (one stream's draws)."""
+    out = np.zeros(3, dtype=np.int64)
+    lib().or_acceptance_trial(kind, seed, float(beta), n, _ptr(out))
+    return out
+
+
+def accept(u: int, d: int, thr: np.ndarray) -> bool:
+    thr = np.ascontiguousarray(thr, dtype=np.uint32)
+    return bool(lib().or_accept(int(u), int(d), _ptr(thr)))
+
+
+class OracleSim:
+    """One lattice with its coupling sample, spins and RNG streams."""
+
+    def __init__(self, L: int, seed_J: int, seed_spin: int, beta: float, kind: int):
+        self._h = lib().or_create(L, seed_J, seed_spin, float(beta), kind)
+        if not self._h:
+            raise ValueError("oracle: invalid arguments L=%r beta=%r kind=%r" % (L, beta, kind))
+        self.L, self.N, self.kind, self.beta = L, L ** 3, kind, beta
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().or_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def sweep(self, n: int = 1, threads: int = 1):
+        lib().or_sweep(self._h, n, threads)
+
+    def energy(self) -> int:
+        return int(lib().or_energy(self._h))
+
+    def tracked_energy(self) -> int:
+        return int(lib().or_tracked_energy(self._h))
+
+    def overlap(self, other: "OracleSim") -> int:
+        return int(lib().or_overlap(self._h, other._h))
+
+    def hash(self) -> int:
+        return int(lib().or_hash(self._h))
+
+    def draws_done(self, t: int) -> int:
+        return int(lib().or_draws_per_stream_done(self._h, t))
+
+    def move_counts(self):
+        att = np.zeros(7, dtype=np.int64)
+        acc = np.zeros(7, dtype=np.int64)
+        lib().or_move_counts(self._h, _ptr(att), _ptr(acc))
+        return att, acc
+
+    def spins(self) -> np.ndarray:
+        out = np.empty(self.N, dtype=np.int8)
+        lib().or_get_spins(self._h, _ptr(out))
+        return out
+
+    def set_spins(self, s: np.ndarray):
+        s = np.ascontiguousarray(s, dtype=np.int8).reshape(-1)
+        assert s.size == self.N
+        lib().or_set_spins(self._h, _ptr(s))
+
+    def couplings(self) -> np.ndarray:
+        out = np.empty(3 * self.N, dtype=np.int8)
+        lib().or_get_couplings(self._h, _ptr(out))
+        return out.reshape(3, self.N)
+
+    def set_couplings(self, J: np.ndarray):
+        J = np.ascontiguousarray(J, dtype=np.int8).reshape(-1)
+        assert J.size == 3 * self.N
+        lib().or_set_couplings(self._h, _ptr(J))
