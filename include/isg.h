@@ -1,0 +1,163 @@
+/*
+ * isg.h -- C-ABI of the GB300 (sm_103a) checkerboard Metropolis engine for the
+ * 3D Edwards-Anderson +-J spin glass (Lulli, Bernaschi, Parisi, arXiv:1411.0127).
+ *
+ * Model and update rule
+ *   H = -sum_<ik> J_ik s_i s_k on an L x L x L periodic cubic lattice (Sec. 1,
+ *   Eq. 1), J_ik = +-1 with probability 1/2 (Eq. 2).  A sweep updates the "red"
+ *   sites (x+y+z even) and then the "blue" ones (Sec. 1); an attempt with u
+ *   unsatisfied bonds has dE = 12 - 4u and flips when u >= 3 or when its own
+ *   32-bit draw d satisfies d < floor(2^32 exp(-beta dE)) (Sec. 4).  Spins and
+ *   couplings are stored one bit each (Sec. 4 bit map: s = +1 -> 1,
+ *   J = -1 -> 1), colour by colour, in row-major bit planes.
+ *
+ * Conventions of every call
+ *   - Every function returns ISG_OK (0) or a negative ISG_ERR_* code and never
+ *     throws.  isg_last_error() returns a message for the calling thread.
+ *   - `cuda_stream` is a cudaStream_t owned by the caller (NULL = the legacy
+ *     default stream).  Calls marked "async" only enqueue work on it; calls
+ *     marked "sync" enqueue, then wait for that stream.
+ *   - Device memory comes from the allocator installed with isg_set_allocator
+ *     (cudaMalloc/cudaFree by default) and stays owned by the handle until
+ *     isg_destroy / isg_batch_destroy.
+ *   - Host pointers are plain pageable or pinned host memory owned by the
+ *     caller; they are only accessed during the call.
+ *   - Site order of host arrays: i = x + L*y + L*L*z.  Coupling arrays hold
+ *     3*N values, direction-major: [d][i], d = 0 (x), 1 (y), 2 (z), where
+ *     J[d][i] joins site i and its +d neighbour.
+ *   - A handle may be used by one host thread at a time.
+ */
+#ifndef ISG_H
+#define ISG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    ISG_OK = 0,
+    ISG_ERR_ARG = -1,      /* invalid argument (nothing was changed) */
+    ISG_ERR_NOMEM = -2,    /* the allocator returned NULL */
+    ISG_ERR_CUDA = -3,     /* a CUDA runtime call failed (message has the name) */
+    ISG_ERR_TIMEOUT = -4,  /* a bounded device wait gave up (device error word) */
+    ISG_ERR_MISMATCH = -5, /* two handles do not describe the same sample */
+    ISG_ERR_STATE = -6     /* call not valid in the handle's current state */
+};
+
+enum { ISG_RNG_MINSTD = 0, ISG_RNG_MT19937 = 1 };
+
+typedef struct isg_sim isg_sim;
+
+/* ---------------------------------------------------------------- setup --- */
+
+/* Create one lattice (sync on the legacy default stream).
+ *   L          even, 4 <= L <= 2048 (else ISG_ERR_ARG)
+ *   seed_J     coupling sample: J_d(i) from the SplitMix64 counter hash
+ *   seed_spin  initial spins and the RNG streams of this replica
+ *   beta       inverse temperature, > 0, may be +INFINITY; 0, negative or NaN
+ *              give ISG_ERR_ARG (beta = 0 would need a threshold of 2^32)
+ *   rng_kind   ISG_RNG_MINSTD (Sec. 3 Lehmer generator) or ISG_RNG_MT19937
+ * Cites: Eq. 1-2 (model), Sec. 4 (threshold table), Sec. 3 (generators). */
+int isg_create(int L, uint64_t seed_J, uint64_t seed_spin, double beta, int rng_kind,
+               isg_sim **out);
+
+/* Free every device buffer of the handle (NULL is ignored). */
+void isg_destroy(isg_sim *h);
+
+/* Install the device allocator used by every later allocation: alloc(size, ctx)
+ * returns device memory or NULL, free(ptr, ctx) releases it.  Passing NULL for
+ * both restores cudaMalloc/cudaFree.  Handles keep the allocator they were
+ * created with. */
+int isg_set_allocator(void *(*alloc)(size_t size, void *ctx),
+                      void (*free_fn)(void *ptr, void *ctx), void *ctx);
+
+/* Message of the last failed call made by this thread ("" if none). */
+const char *isg_last_error(void);
+
+/* Geometry of a handle: L, word width in bits (32 or 64), words per row and
+ * colour, number of RNG streams and rows per stream.  Any pointer may be NULL. */
+int isg_info(const isg_sim *h, int *L, int *word_bits, int *words_per_row,
+             int64_t *streams, int64_t *rows_per_stream);
+
+/* ---------------------------------------------------------------- sweep --- */
+
+/* Enqueue n full sweeps (red pass, then blue pass) on cuda_stream (async).
+ * n >= 0.  The fused energy change of every accepted flip is accumulated on the
+ * device (read with isg_tracked_energy).  Sec. 1 (colour order), Sec. 4 (rule). */
+int isg_sweep(isg_sim *h, int64_t n, void *cuda_stream);
+
+/* Same as isg_sweep but with the plain per-colour kernel: one stream per warp,
+ * draws and bit logic in separate phases, no persistence.  Results are
+ * bit-identical to isg_sweep; it is kept as the comparison kernel. */
+int isg_sweep_plain(isg_sim *h, int64_t n, void *cuda_stream);
+
+/* Number of sweeps done since creation (or since the loaded checkpoint). */
+int isg_sweeps_done(const isg_sim *h, int64_t *n);
+
+/* ------------------------------------------------------------- measures --- */
+
+/* E = -sum_<ik> J_ik s_i s_k from scratch (sync).  Eq. 1. */
+int isg_energy(isg_sim *h, int64_t *E, void *cuda_stream);
+
+/* Initial energy plus the sum of accepted dE of every sweep so far (sync on
+ * the stream of the last sweep).  Equals isg_energy when the kernels are right. */
+int isg_tracked_energy(isg_sim *h, int64_t *E);
+
+/* Q = sum_i s^a_i s^b_i (sync).  a and b must have the same L and seed_J, else
+ * ISG_ERR_MISMATCH.  q = Q/N is the replica overlap. */
+int isg_overlap(const isg_sim *a, const isg_sim *b, int64_t *Q, void *cuda_stream);
+
+/* Zobrist hash H = XOR over sites with s_i = +1 of SplitMix64(0xA54FF53A5F1D36F1, i)
+ * (sync).  Equal configurations give equal hashes. */
+int isg_hash(const isg_sim *h, uint64_t *H, void *cuda_stream);
+
+/* Copy the spins to host_out as int8 +-1 in site order (sync).  n must be
+ * at least L^3 (else ISG_ERR_ARG). */
+int isg_read_spins(const isg_sim *h, int8_t *host_out, size_t n, void *cuda_stream);
+
+/* Overwrite the spins from a host int8 array of +-1 in site order (sync); the
+ * tracked energy restarts from the new configuration.  Any value other than
+ * +1 or -1 gives ISG_ERR_ARG and changes nothing. */
+int isg_write_spins(isg_sim *h, const int8_t *host_in, size_t n, void *cuda_stream);
+
+/* Copy the couplings to host_out as int8 +-1, [d][i] (sync); n >= 3 L^3. */
+int isg_read_couplings(const isg_sim *h, int8_t *host_out, size_t n, void *cuda_stream);
+
+/* Overwrite the couplings from a host int8 +-1 array [d][i] (sync); the
+ * tracked energy restarts.  Other values give ISG_ERR_ARG. */
+int isg_write_couplings(isg_sim *h, const int8_t *host_in, size_t n, void *cuda_stream);
+
+/* ----------------------------------------------------------- checkpoint --- */
+
+/* Serialise the whole state (spins, couplings, RNG streams with their
+ * positions, sweep count, energy bookkeeping, parameters) into host_buf (sync).
+ * With host_buf == NULL only *n is set to the size needed.  If *n is smaller
+ * than needed, ISG_ERR_ARG and *n = size needed. */
+int isg_save(const isg_sim *h, void *host_buf, size_t *n, void *cuda_stream);
+
+/* Create a new handle from a buffer written by isg_save (sync).  A corrupt or
+ * truncated buffer gives ISG_ERR_ARG.  Continuing the loaded handle gives the
+ * same trajectory, bit for bit, as continuing the saved one. */
+int isg_load(const void *host_buf, size_t n, isg_sim **out);
+
+/* ------------------------------------------------------------- testing --- */
+
+/* Run the device flip rule on n stencils (sync).  code[j] bits: 0 = spin bit,
+ * 1..6 = neighbour spin bits, 7..12 = coupling bits (Sec. 4 bit map; bond k
+ * joins the site and neighbour k).  draw[j] is the attempt's 32-bit draw.
+ * Writes flip[j] = 1 when the kernel's bit logic flips the spin, and u[j] = its
+ * count of unsatisfied bonds.  thr = {thr1, thr2, thr3}.  Host arrays. */
+int isg_stencil_decisions(const uint16_t *code, const uint32_t *draw, int64_t n,
+                          const uint32_t thr[3], uint8_t *flip, uint8_t *u);
+
+/* First n draws of stream t of the handle's generator, from its current
+ * position, without advancing it (sync); host_out gets the 32-bit draws. */
+int isg_peek_draws(const isg_sim *h, int64_t t, int64_t n, uint32_t *host_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ISG_H */

@@ -71,6 +71,7 @@ def lib() -> ctypes.CDLL:
             "or_set_couplings": (None, [vp, vp]),
             "or_move_counts": (None, [vp, vp, vp]),
             "or_acceptance_trial": (None, [i32, u32, dbl, i64, vp]),
+            "or_peek_draws": (None, [vp, i64, i64, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -166,6 +167,11 @@ class OracleSim:
 
     def draws_done(self, t: int) -> int:
         return int(lib().or_draws_per_stream_done(self._h, t))
+
+    def peek_draws(self, t: int, n: int) -> np.ndarray:
+        out = np.empty(n, dtype=np.uint32)
+        lib().or_peek_draws(self._h, t, n, _ptr(out))
+        return out
 
     def move_counts(self):
         att = np.zeros(7, dtype=np.int64)

@@ -382,6 +382,13 @@ void or_move_counts(const or_sim *o, int64_t attempts[7], int64_t accepts[7])
     }
 }
 
+void or_peek_draws(const or_sim *o, int64_t t, int64_t n, uint32_t *out)
+{
+    if (t < 0 || t >= o->S) return;
+    stream_t copy = o->st[t];
+    for (int64_t k = 0; k < n; ++k) out[k] = stream_draw(&copy);
+}
+
 void or_acceptance_trial(int kind, uint32_t seed, double beta, int64_t n, int64_t accepts[3])
 {
     uint32_t thr[4];

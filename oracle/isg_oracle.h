@@ -70,6 +70,8 @@ void    or_get_couplings(const or_sim *s, int8_t *out);   /* 3N values, [d][i], 
 void    or_set_couplings(or_sim *s, const int8_t *in);    /* resets the tracked energy */
 /* Per-u tallies of the sweeps so far: attempts[u], accepts[u], u = 0..6. */
 void    or_move_counts(const or_sim *s, int64_t attempts[7], int64_t accepts[7]);
+/* The next n draws of stream t, without advancing it. */
+void    or_peek_draws(const or_sim *s, int64_t t, int64_t n, uint32_t *out);
 /* n Metropolis decisions for each u = 0,1,2 with draws from one stream of the
  * given kind and seed word (MT19937: init_genrand(seed); MINSTD: x0 = seed). */
 void    or_acceptance_trial(int kind, uint32_t seed, double beta, int64_t n, int64_t accepts[3]);

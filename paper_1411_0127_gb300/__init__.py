@@ -1,0 +1,255 @@
+"""Python binding of ``libisg.so``, the GB300 checkerboard Metropolis engine for
+the 3D Edwards-Anderson +-J spin glass (arXiv:1411.0127).
+
+This module only marshals arguments to the C-ABI declared in ``include/isg.h``;
+every step of the sweep runs in the CUDA kernels of ``csrc/``.  PyTorch, when
+present, provides the device allocator (its caching allocator) and streams.
+If ``libisg.so`` is missing the import of the library fails loudly: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libisg.so")
+
+ISG_OK, ISG_ERR_ARG, ISG_ERR_NOMEM, ISG_ERR_CUDA, ISG_ERR_TIMEOUT, ISG_ERR_MISMATCH, ISG_ERR_STATE = \
+    0, -1, -2, -3, -4, -5, -6
+ISG_RNG_MINSTD, ISG_RNG_MT19937 = 0, 1
+RNG_KINDS = {"minstd": ISG_RNG_MINSTD, "mt19937": ISG_RNG_MT19937}
+
+_vp, _i32, _i64, _u64, _dbl, _sz = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64,
+                                    ctypes.c_double, ctypes.c_size_t)
+_PP = ctypes.POINTER(ctypes.c_void_p)
+
+# name -> (restype, argtypes); every name here is declared in include/isg.h
+SIGNATURES = {
+    "isg_create": (_i32, [_i32, _u64, _u64, _dbl, _i32, _PP]),
+    "isg_destroy": (None, [_vp]),
+    "isg_set_allocator": (_i32, [_vp, _vp, _vp]),
+    "isg_last_error": (ctypes.c_char_p, []),
+    "isg_info": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "isg_sweep": (_i32, [_vp, _i64, _vp]),
+    "isg_sweep_plain": (_i32, [_vp, _i64, _vp]),
+    "isg_sweeps_done": (_i32, [_vp, _vp]),
+    "isg_energy": (_i32, [_vp, _vp, _vp]),
+    "isg_tracked_energy": (_i32, [_vp, _vp]),
+    "isg_overlap": (_i32, [_vp, _vp, _vp, _vp]),
+    "isg_hash": (_i32, [_vp, _vp, _vp]),
+    "isg_read_spins": (_i32, [_vp, _vp, _sz, _vp]),
+    "isg_write_spins": (_i32, [_vp, _vp, _sz, _vp]),
+    "isg_read_couplings": (_i32, [_vp, _vp, _sz, _vp]),
+    "isg_write_couplings": (_i32, [_vp, _vp, _sz, _vp]),
+    "isg_save": (_i32, [_vp, _vp, _vp, _vp]),
+    "isg_load": (_i32, [_vp, _sz, _PP]),
+    "isg_stencil_decisions": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp]),
+    "isg_peek_draws": (_i32, [_vp, _i64, _i64, _vp]),
+}
+
+
+class IsgError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("isg error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libisg.so (built by ``__graft_entry__.build()``); raises if missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libisg.so is not built (%s); run `python -c 'import __graft_entry__ as g; "
+                               "g.build()'` -- there is no CPU fallback" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != ISG_OK:
+        raise IsgError(rc, lib().isg_last_error().decode(errors="replace"))
+
+
+def _stream(stream) -> int:
+    """cudaStream_t of a torch stream, an int handle, or the current torch stream."""
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _ptr(a: np.ndarray) -> int:
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data
+
+
+# ------------------------------------------------------------- allocator ---
+_ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+_keep = []
+
+
+def use_torch_allocator():
+    """Route the library's device allocations through torch's caching allocator."""
+    import torch
+
+    def _alloc(size, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(size))
+        except Exception:
+            return None
+
+    def _free(ptr, ctx):
+        if ptr:
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+    a, f = _ALLOC_T(_alloc), _FREE_T(_free)
+    _keep[:] = [a, f]
+    _check(lib().isg_set_allocator(ctypes.cast(a, ctypes.c_void_p), ctypes.cast(f, ctypes.c_void_p), None))
+
+
+def use_default_allocator():
+    _check(lib().isg_set_allocator(None, None, None))
+
+
+# ---------------------------------------------------------------- handle ---
+class Sim:
+    """One L^3 lattice (one replica): couplings, bit-packed spins, RNG streams."""
+
+    def __init__(self, L: int, seed_J: int, seed_spin: int, beta: float, rng_kind="minstd", *, _handle=None):
+        kind = RNG_KINDS[rng_kind] if isinstance(rng_kind, str) else int(rng_kind)
+        if _handle is None:
+            h = ctypes.c_void_p()
+            _check(lib().isg_create(int(L), int(seed_J) & (2**64 - 1), int(seed_spin) & (2**64 - 1),
+                                    float(beta), kind, ctypes.byref(h)))
+            _handle = h.value
+        self._h = _handle
+        self.L, self.N, self.kind, self.beta = int(L), int(L) ** 3, kind, float(beta)
+
+    @property
+    def handle(self) -> int:
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().isg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        L, wb, W = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        S, R = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().isg_info(self._h, ctypes.byref(L), ctypes.byref(wb), ctypes.byref(W), ctypes.byref(S),
+                              ctypes.byref(R)))
+        return {"L": L.value, "word_bits": wb.value, "words_per_row": W.value, "streams": S.value,
+                "rows_per_stream": R.value}
+
+    def sweep(self, n: int = 1, stream=None):
+        _check(lib().isg_sweep(self._h, int(n), _stream(stream)))
+
+    def sweep_plain(self, n: int = 1, stream=None):
+        _check(lib().isg_sweep_plain(self._h, int(n), _stream(stream)))
+
+    def sweeps_done(self) -> int:
+        v = ctypes.c_int64()
+        _check(lib().isg_sweeps_done(self._h, ctypes.byref(v)))
+        return v.value
+
+    def energy(self, stream=None) -> int:
+        v = ctypes.c_int64()
+        _check(lib().isg_energy(self._h, ctypes.byref(v), _stream(stream)))
+        return v.value
+
+    def tracked_energy(self) -> int:
+        v = ctypes.c_int64()
+        _check(lib().isg_tracked_energy(self._h, ctypes.byref(v)))
+        return v.value
+
+    def overlap(self, other: "Sim", stream=None) -> int:
+        v = ctypes.c_int64()
+        _check(lib().isg_overlap(self._h, other._h, ctypes.byref(v), _stream(stream)))
+        return v.value
+
+    def hash(self, stream=None) -> int:
+        v = ctypes.c_uint64()
+        _check(lib().isg_hash(self._h, ctypes.byref(v), _stream(stream)))
+        return v.value
+
+    def read_spins(self, stream=None) -> np.ndarray:
+        out = np.empty(self.N, dtype=np.int8)
+        _check(lib().isg_read_spins(self._h, _ptr(out), out.size, _stream(stream)))
+        return out
+
+    def write_spins(self, s: np.ndarray, stream=None):
+        s = np.ascontiguousarray(s, dtype=np.int8).reshape(-1)
+        _check(lib().isg_write_spins(self._h, _ptr(s), s.size, _stream(stream)))
+
+    def read_couplings(self, stream=None) -> np.ndarray:
+        out = np.empty(3 * self.N, dtype=np.int8)
+        _check(lib().isg_read_couplings(self._h, _ptr(out), out.size, _stream(stream)))
+        return out.reshape(3, self.N)
+
+    def write_couplings(self, J: np.ndarray, stream=None):
+        J = np.ascontiguousarray(J, dtype=np.int8).reshape(-1)
+        _check(lib().isg_write_couplings(self._h, _ptr(J), J.size, _stream(stream)))
+
+    def save(self, stream=None) -> bytes:
+        n = ctypes.c_size_t(0)
+        _check(lib().isg_save(self._h, None, ctypes.byref(n), _stream(stream)))
+        buf = ctypes.create_string_buffer(n.value)
+        _check(lib().isg_save(self._h, buf, ctypes.byref(n), _stream(stream)))
+        return buf.raw[:n.value]
+
+    @classmethod
+    def load(cls, data: bytes) -> "Sim":
+        h = ctypes.c_void_p()
+        buf = ctypes.create_string_buffer(data, len(data))
+        _check(lib().isg_load(buf, len(data), ctypes.byref(h)))
+        sim = cls.__new__(cls)
+        sim._h = h.value
+        L = ctypes.c_int()
+        _check(lib().isg_info(sim._h, ctypes.byref(L), None, None, None, None))
+        sim.L, sim.N = L.value, L.value ** 3
+        sim.kind, sim.beta = None, None
+        return sim
+
+    def peek_draws(self, t: int, n: int) -> np.ndarray:
+        out = np.empty(n, dtype=np.uint32)
+        _check(lib().isg_peek_draws(self._h, int(t), int(n), _ptr(out)))
+        return out
+
+
+def stencil_decisions(codes: np.ndarray, draws: np.ndarray, thr) -> tuple[np.ndarray, np.ndarray]:
+    """Device bit logic on explicit stencils (see isg_stencil_decisions)."""
+    codes = np.ascontiguousarray(codes, dtype=np.uint16)
+    draws = np.ascontiguousarray(draws, dtype=np.uint32)
+    t = np.ascontiguousarray(thr, dtype=np.uint32)
+    assert codes.size == draws.size and t.size == 3
+    flip = np.empty(codes.size, dtype=np.uint8)
+    u = np.empty(codes.size, dtype=np.uint8)
+    _check(lib().isg_stencil_decisions(_ptr(codes), _ptr(draws), codes.size, _ptr(t), _ptr(flip), _ptr(u)))
+    return flip, u

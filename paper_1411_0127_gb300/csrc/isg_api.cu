@@ -1,0 +1,463 @@
+// isg_api.cu -- the extern "C" boundary (include/isg.h): argument checks,
+// allocation through the installed allocator, kernel launches, status codes.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "isg_common.cuh"
+
+namespace isg {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    set_error("%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+    return ISG_ERR_CUDA;
+}
+
+static void* default_alloc(size_t n, void*) {
+    void* p = nullptr;
+    return cudaMalloc(&p, n) == cudaSuccess ? p : nullptr;
+}
+static void default_free(void* p, void*) { cudaFree(p); }
+
+static std::mutex g_alloc_mu;
+static void* (*g_alloc)(size_t, void*) = default_alloc;
+static void (*g_free)(void*, void*) = default_free;
+static void* g_alloc_ctx = nullptr;
+
+void* dev_alloc(isg_sim* h, size_t n) { return h->alloc(n ? n : 1, h->alloc_ctx); }
+void dev_free(isg_sim* h, void* p) {
+    if (p) h->free_fn(p, h->alloc_ctx);
+}
+
+// floor(2^32 exp(-4 k beta)), k = 1..3 (Sec. 4, Rmax exp(-beta dE)).
+static void thresholds(double beta, uint32_t thr[4]) {
+    thr[0] = 0;
+    for (int k = 1; k <= 3; ++k) {
+        const double v = std::floor(4294967296.0 * std::exp(-4.0 * k * beta));
+        thr[k] = v <= 0.0 ? 0u : (v >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)v);
+    }
+}
+
+// Stream partition: S0 = clamp(L^3 / 32768, 1, 8192); R = ceil(L^2 / S0).
+static void partition(int L, int64_t* R, int64_t* S) {
+    const int64_t rows = (int64_t)L * L;
+    int64_t s0 = (int64_t)L * L * L / 32768;
+    s0 = s0 < 1 ? 1 : (s0 > 8192 ? 8192 : s0);
+    *R = (rows + s0 - 1) / s0;
+    *S = (rows + *R - 1) / *R;
+}
+
+static bool beta_ok(double beta) { return beta > 0.0; }  // false for 0, negatives, NaN
+
+// Fill the geometry fields and allocate every device buffer (zeroed).
+static int alloc_sim(isg_sim* h) {
+    h->half = h->L / 2;
+    const int w64 = (h->half + 63) / 64, w32 = (h->half + 31) / 32;
+    h->wbits = (2 * w64 == w32) ? 64 : 32;
+    h->W = (h->half + h->wbits - 1) / h->wbits;
+    h->nt = h->half - (h->W - 1) * h->wbits;
+    h->rows = (int64_t)h->L * h->L;
+    partition(h->L, &h->R, &h->S);
+    const int64_t raw = h->rows * h->W * (h->wbits / 8);
+    h->plane_bytes = (raw + 255) / 256 * 256;
+    const size_t pbytes = (size_t)h->plane_bytes * 8;
+    h->planes = (unsigned char*)dev_alloc(h, pbytes);
+    const size_t rng_words = h->kind == ISG_RNG_MT19937 ? (size_t)h->S * kMtN : (size_t)h->S;
+    h->rng = (uint32_t*)dev_alloc(h, rng_words * 4);
+    h->rng_pos = (uint32_t*)dev_alloc(h, (size_t)h->S * 4);
+    h->scal = (long long*)dev_alloc(h, 8 * sizeof(long long));
+    if (!h->planes || !h->rng || !h->rng_pos || !h->scal) {
+        set_error("isg: device allocation failed (%zu bytes of planes)", pbytes);
+        return ISG_ERR_NOMEM;
+    }
+    cudaError_t e = cudaMemset(h->planes, 0, pbytes);
+    if (e == cudaSuccess) e = cudaMemset(h->scal, 0, 8 * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMemset(h->rng_pos, 0, (size_t)h->S * 4);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
+    return ISG_OK;
+}
+
+static void free_sim(isg_sim* h) {
+    if (!h) return;
+    dev_free(h, h->planes);
+    dev_free(h, h->rng);
+    dev_free(h, h->rng_pos);
+    dev_free(h, h->scal);
+    delete h;
+}
+
+static isg_sim* new_sim() {
+    isg_sim* h = new (std::nothrow) isg_sim();
+    if (!h) return nullptr;
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    h->alloc = g_alloc;
+    h->free_fn = g_free;
+    h->alloc_ctx = g_alloc_ctx;
+    return h;
+}
+
+// Energy from scratch into *E, on stream s (sync).
+static int energy_sync(const isg_sim* h, int64_t* E, cudaStream_t s) {
+    long long* acc = h->scal + 1;
+    cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(long long), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    e = launch_energy(h, acc, s);
+    if (e != cudaSuccess) return cuda_fail(e, "energy kernel launch");
+    long long U = 0;
+    e = cudaMemcpyAsync(&U, acc, sizeof U, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "energy");
+    *E = 2 * (int64_t)U - 3 * (int64_t)h->L * h->L * h->L;
+    return ISG_OK;
+}
+
+// Restart the energy bookkeeping from the current configuration.
+static int restart_tracking(isg_sim* h, cudaStream_t s) {
+    int rc = energy_sync(h, &h->E0, s);
+    if (rc) return rc;
+    cudaError_t e = cudaMemsetAsync(h->scal, 0, sizeof(long long), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? ISG_OK : cuda_fail(e, "reset tracked energy");
+}
+
+}  // namespace isg
+
+using namespace isg;
+
+extern "C" {
+
+const char* isg_last_error(void) { return g_err; }
+
+int isg_set_allocator(void* (*alloc)(size_t, void*), void (*free_fn)(void*, void*), void* ctx) {
+    if ((alloc == nullptr) != (free_fn == nullptr)) {
+        set_error("isg_set_allocator: give both functions or neither");
+        return ISG_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc = alloc ? alloc : default_alloc;
+    g_free = free_fn ? free_fn : default_free;
+    g_alloc_ctx = alloc ? ctx : nullptr;
+    return ISG_OK;
+}
+
+int isg_create(int L, uint64_t seed_J, uint64_t seed_spin, double beta, int rng_kind, isg_sim** out) {
+    if (!out) { set_error("isg_create: out is NULL"); return ISG_ERR_ARG; }
+    *out = nullptr;
+    if (L < 4 || L > 2048 || (L & 1)) { set_error("isg_create: L=%d must be even and in [4, 2048]", L); return ISG_ERR_ARG; }
+    if (!beta_ok(beta)) { set_error("isg_create: beta must be > 0 (got %g)", beta); return ISG_ERR_ARG; }
+    if (rng_kind != ISG_RNG_MINSTD && rng_kind != ISG_RNG_MT19937) {
+        set_error("isg_create: unknown rng_kind %d", rng_kind);
+        return ISG_ERR_ARG;
+    }
+    isg_sim* h = new_sim();
+    if (!h) { set_error("isg_create: out of host memory"); return ISG_ERR_NOMEM; }
+    h->L = L;
+    h->kind = rng_kind;
+    h->beta = beta;
+    h->seed_J = seed_J;
+    h->seed_spin = seed_spin;
+    thresholds(beta, h->thr);
+    int rc = alloc_sim(h);
+    if (rc) { free_sim(h); return rc; }
+    cudaError_t e = launch_init_planes(h, 0);
+    if (e == cudaSuccess) e = launch_init_rng(h, 0);
+    if (e != cudaSuccess) { free_sim(h); return cuda_fail(e, "init kernels"); }
+    rc = restart_tracking(h, 0);
+    if (rc) { free_sim(h); return rc; }
+    *out = h;
+    return ISG_OK;
+}
+
+void isg_destroy(isg_sim* h) {
+    if (!h) return;
+    cudaDeviceSynchronize();
+    free_sim(h);
+}
+
+int isg_info(const isg_sim* h, int* L, int* word_bits, int* words_per_row, int64_t* streams,
+             int64_t* rows_per_stream) {
+    if (!h) { set_error("isg_info: NULL handle"); return ISG_ERR_ARG; }
+    if (L) *L = h->L;
+    if (word_bits) *word_bits = h->wbits;
+    if (words_per_row) *words_per_row = h->W;
+    if (streams) *streams = h->S;
+    if (rows_per_stream) *rows_per_stream = h->R;
+    return ISG_OK;
+}
+
+int isg_sweep_plain(isg_sim* h, int64_t n, void* stream) {
+    if (!h || n < 0) { set_error("isg_sweep_plain: bad handle or n"); return ISG_ERR_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int64_t k = 0; k < n; ++k) {
+        cudaError_t e = launch_flip_plain(h, 0, s);
+        if (e == cudaSuccess) e = launch_flip_plain(h, 1, s);
+        if (e != cudaSuccess) return cuda_fail(e, "flip kernel launch");
+    }
+    h->sweeps += n;
+    h->last_stream = s;
+    return ISG_OK;
+}
+
+int isg_sweep(isg_sim* h, int64_t n, void* stream) {
+    if (!h || n < 0) { set_error("isg_sweep: bad handle or n"); return ISG_ERR_ARG; }
+    return isg_sweep_plain(h, n, stream);
+}
+
+int isg_sweeps_done(const isg_sim* h, int64_t* n) {
+    if (!h || !n) { set_error("isg_sweeps_done: NULL argument"); return ISG_ERR_ARG; }
+    *n = h->sweeps;
+    return ISG_OK;
+}
+
+int isg_energy(isg_sim* h, int64_t* E, void* stream) {
+    if (!h || !E) { set_error("isg_energy: NULL argument"); return ISG_ERR_ARG; }
+    return energy_sync(h, E, (cudaStream_t)stream);
+}
+
+int isg_tracked_energy(isg_sim* h, int64_t* E) {
+    if (!h || !E) { set_error("isg_tracked_energy: NULL argument"); return ISG_ERR_ARG; }
+    long long d = 0;
+    cudaError_t e = cudaMemcpyAsync(&d, h->scal, sizeof d, cudaMemcpyDeviceToHost, h->last_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->last_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "isg_tracked_energy");
+    *E = h->E0 + (int64_t)d;
+    return ISG_OK;
+}
+
+int isg_overlap(const isg_sim* a, const isg_sim* b, int64_t* Q, void* stream) {
+    if (!a || !b || !Q) { set_error("isg_overlap: NULL argument"); return ISG_ERR_ARG; }
+    if (a->L != b->L || a->seed_J != b->seed_J) {
+        set_error("isg_overlap: handles differ in L or seed_J");
+        return ISG_ERR_MISMATCH;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    long long* acc = a->scal + 1;
+    cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(long long), s);
+    if (e == cudaSuccess) e = launch_overlap(a, b, acc, s);
+    long long nd = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nd, acc, sizeof nd, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "isg_overlap");
+    *Q = (int64_t)a->L * a->L * a->L - 2 * (int64_t)nd;
+    return ISG_OK;
+}
+
+int isg_hash(const isg_sim* h, uint64_t* H, void* stream) {
+    if (!h || !H) { set_error("isg_hash: NULL argument"); return ISG_ERR_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long* acc = (unsigned long long*)(h->scal + 2);
+    cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = launch_hash(h, acc, s);
+    unsigned long long v = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&v, acc, sizeof v, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "isg_hash");
+    *H = (uint64_t)v;
+    return ISG_OK;
+}
+
+// Host <-> device transfer of an int8 array through a temporary device buffer.
+static int read_int8(const isg_sim* hc, int8_t* out, size_t n, size_t need, cudaStream_t s, bool couplings) {
+    isg_sim* h = const_cast<isg_sim*>(hc);
+    if (n < need) { set_error("read: buffer holds %zu values, %zu needed", n, need); return ISG_ERR_ARG; }
+    int8_t* d = (int8_t*)dev_alloc(h, need);
+    if (!d) { set_error("read: device allocation failed"); return ISG_ERR_NOMEM; }
+    cudaError_t e = couplings ? launch_unpack_couplings(h, d, s) : launch_unpack_spins(h, d, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, need, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dev_free(h, d);
+    return e == cudaSuccess ? ISG_OK : cuda_fail(e, "read");
+}
+
+static int write_int8(isg_sim* h, const int8_t* in, size_t n, size_t need, cudaStream_t s, bool couplings) {
+    if (n < need) { set_error("write: buffer holds %zu values, %zu needed", n, need); return ISG_ERR_ARG; }
+    int8_t* d = (int8_t*)dev_alloc(h, need);
+    int* bad = (int*)dev_alloc(h, sizeof(int));
+    if (!d || !bad) {
+        dev_free(h, d);
+        dev_free(h, bad);
+        set_error("write: device allocation failed");
+        return ISG_ERR_NOMEM;
+    }
+    int hbad = 0;
+    cudaError_t e = cudaMemcpyAsync(d, in, need, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = launch_check_pm1(d, (int64_t)need, bad, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && !hbad) {
+        e = couplings ? launch_pack_couplings(h, d, s) : launch_pack_spins(h, d, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    dev_free(h, d);
+    dev_free(h, bad);
+    if (e != cudaSuccess) return cuda_fail(e, "write");
+    if (hbad) { set_error("write: values must be +1 or -1"); return ISG_ERR_ARG; }
+    return restart_tracking(h, s);
+}
+
+int isg_read_spins(const isg_sim* h, int8_t* out, size_t n, void* stream) {
+    if (!h || !out) { set_error("isg_read_spins: NULL argument"); return ISG_ERR_ARG; }
+    return read_int8(h, out, n, (size_t)h->L * h->L * h->L, (cudaStream_t)stream, false);
+}
+
+int isg_write_spins(isg_sim* h, const int8_t* in, size_t n, void* stream) {
+    if (!h || !in) { set_error("isg_write_spins: NULL argument"); return ISG_ERR_ARG; }
+    return write_int8(h, in, n, (size_t)h->L * h->L * h->L, (cudaStream_t)stream, false);
+}
+
+int isg_read_couplings(const isg_sim* h, int8_t* out, size_t n, void* stream) {
+    if (!h || !out) { set_error("isg_read_couplings: NULL argument"); return ISG_ERR_ARG; }
+    return read_int8(h, out, n, 3 * (size_t)h->L * h->L * h->L, (cudaStream_t)stream, true);
+}
+
+int isg_write_couplings(isg_sim* h, const int8_t* in, size_t n, void* stream) {
+    if (!h || !in) { set_error("isg_write_couplings: NULL argument"); return ISG_ERR_ARG; }
+    return write_int8(h, in, n, 3 * (size_t)h->L * h->L * h->L, (cudaStream_t)stream, true);
+}
+
+// ---------------------------------------------------------------- checkpoint
+struct SaveHeader {
+    char magic[8];
+    uint32_t version, L, kind, wbits;
+    double beta;
+    uint64_t seed_J, seed_spin;
+    int64_t R, S, sweeps, E0, dE, plane_bytes, rng_words;
+};
+
+static const char kMagic[8] = {'I', 'S', 'G', 'C', 'K', 'P', 'T', '1'};
+
+int isg_save(const isg_sim* h, void* buf, size_t* n, void* stream) {
+    if (!h || !n) { set_error("isg_save: NULL argument"); return ISG_ERR_ARG; }
+    const size_t rng_words = h->kind == ISG_RNG_MT19937 ? (size_t)h->S * kMtN : (size_t)h->S;
+    const size_t need = sizeof(SaveHeader) + (size_t)h->plane_bytes * 8 + rng_words * 4 + (size_t)h->S * 4;
+    if (!buf) { *n = need; return ISG_OK; }
+    if (*n < need) { *n = need; set_error("isg_save: buffer too small"); return ISG_ERR_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    SaveHeader hd;
+    memset(&hd, 0, sizeof hd);
+    memcpy(hd.magic, kMagic, 8);
+    hd.version = 1;
+    hd.L = (uint32_t)h->L;
+    hd.kind = (uint32_t)h->kind;
+    hd.wbits = (uint32_t)h->wbits;
+    hd.beta = h->beta;
+    hd.seed_J = h->seed_J;
+    hd.seed_spin = h->seed_spin;
+    hd.R = h->R;
+    hd.S = h->S;
+    hd.sweeps = h->sweeps;
+    hd.E0 = h->E0;
+    hd.plane_bytes = h->plane_bytes;
+    hd.rng_words = (int64_t)rng_words;
+    long long d = 0;
+    unsigned char* p = (unsigned char*)buf + sizeof hd;
+    cudaError_t e = cudaStreamSynchronize(h->last_stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&d, h->scal, sizeof d, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p, h->planes, (size_t)h->plane_bytes * 8, cudaMemcpyDeviceToHost, s);
+    p += (size_t)h->plane_bytes * 8;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p, h->rng, rng_words * 4, cudaMemcpyDeviceToHost, s);
+    p += rng_words * 4;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p, h->rng_pos, (size_t)h->S * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "isg_save");
+    hd.dE = d;
+    memcpy(buf, &hd, sizeof hd);
+    *n = need;
+    return ISG_OK;
+}
+
+int isg_load(const void* buf, size_t n, isg_sim** out) {
+    if (!buf || !out) { set_error("isg_load: NULL argument"); return ISG_ERR_ARG; }
+    *out = nullptr;
+    SaveHeader hd;
+    if (n < sizeof hd) { set_error("isg_load: truncated buffer"); return ISG_ERR_ARG; }
+    memcpy(&hd, buf, sizeof hd);
+    if (memcmp(hd.magic, kMagic, 8) != 0 || hd.version != 1) { set_error("isg_load: not a checkpoint"); return ISG_ERR_ARG; }
+    if (hd.L < 4 || hd.L > 2048 || (hd.L & 1) || hd.kind > 1 || !beta_ok(hd.beta)) {
+        set_error("isg_load: corrupt header");
+        return ISG_ERR_ARG;
+    }
+    isg_sim* h = new_sim();
+    if (!h) { set_error("isg_load: out of host memory"); return ISG_ERR_NOMEM; }
+    h->L = (int)hd.L;
+    h->kind = (int)hd.kind;
+    h->beta = hd.beta;
+    h->seed_J = hd.seed_J;
+    h->seed_spin = hd.seed_spin;
+    thresholds(h->beta, h->thr);
+    int rc = alloc_sim(h);
+    if (rc) { free_sim(h); return rc; }
+    const size_t rng_words = h->kind == ISG_RNG_MT19937 ? (size_t)h->S * kMtN : (size_t)h->S;
+    const size_t need = sizeof hd + (size_t)h->plane_bytes * 8 + rng_words * 4 + (size_t)h->S * 4;
+    if (n < need || hd.plane_bytes != h->plane_bytes || hd.S != h->S || hd.R != h->R ||
+        hd.rng_words != (int64_t)rng_words || (int)hd.wbits != h->wbits) {
+        free_sim(h);
+        set_error("isg_load: buffer does not match its header");
+        return ISG_ERR_ARG;
+    }
+    const unsigned char* p = (const unsigned char*)buf + sizeof hd;
+    long long d = hd.dE;
+    cudaError_t e = cudaMemcpy(h->planes, p, (size_t)h->plane_bytes * 8, cudaMemcpyHostToDevice);
+    p += (size_t)h->plane_bytes * 8;
+    if (e == cudaSuccess) e = cudaMemcpy(h->rng, p, rng_words * 4, cudaMemcpyHostToDevice);
+    p += rng_words * 4;
+    if (e == cudaSuccess) e = cudaMemcpy(h->rng_pos, p, (size_t)h->S * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->scal, &d, sizeof d, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { free_sim(h); return cuda_fail(e, "isg_load"); }
+    h->sweeps = hd.sweeps;
+    h->E0 = hd.E0;
+    *out = h;
+    return ISG_OK;
+}
+
+// ------------------------------------------------------------------ testing
+int isg_stencil_decisions(const uint16_t* code, const uint32_t* draw, int64_t n, const uint32_t thr[3],
+                          uint8_t* flip, uint8_t* u) {
+    if (!code || !draw || !thr || !flip || !u || n < 0) { set_error("isg_stencil_decisions: bad argument"); return ISG_ERR_ARG; }
+    if (n == 0) return ISG_OK;
+    uint16_t* dc = nullptr;
+    uint32_t* dd = nullptr;
+    uint8_t *df = nullptr, *du = nullptr;
+    cudaError_t e = cudaMalloc(&dc, n * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&dd, n * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&df, n);
+    if (e == cudaSuccess) e = cudaMalloc(&du, n);
+    if (e == cudaSuccess) e = cudaMemcpy(dc, code, n * 2, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dd, draw, n * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_stencil(dc, dd, n, thr[0], thr[1], thr[2], df, du, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(flip, df, n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(u, du, n, cudaMemcpyDeviceToHost);
+    cudaFree(dc);
+    cudaFree(dd);
+    cudaFree(df);
+    cudaFree(du);
+    return e == cudaSuccess ? ISG_OK : cuda_fail(e, "isg_stencil_decisions");
+}
+
+int isg_peek_draws(const isg_sim* h, int64_t t, int64_t n, uint32_t* out) {
+    if (!h || !out || t < 0 || t >= h->S || n < 0) { set_error("isg_peek_draws: bad argument"); return ISG_ERR_ARG; }
+    if (n == 0) return ISG_OK;
+    isg_sim* hm = const_cast<isg_sim*>(h);
+    uint32_t* d = (uint32_t*)dev_alloc(hm, (size_t)n * 4);
+    if (!d) { set_error("isg_peek_draws: allocation failed"); return ISG_ERR_NOMEM; }
+    cudaError_t e = cudaStreamSynchronize(h->last_stream);
+    if (e == cudaSuccess) e = launch_peek_draws(h, t, n, d, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(out, d, (size_t)n * 4, cudaMemcpyDeviceToHost);
+    dev_free(hm, d);
+    return e == cudaSuccess ? ISG_OK : cuda_fail(e, "isg_peek_draws");
+}
+
+}  // extern "C"
