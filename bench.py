@@ -1,0 +1,368 @@
+#!/usr/bin/env python3
+"""psFlip benchmark of the GB300 checkerboard Metropolis sweep (arXiv:1411.0127).
+
+Workload: one L = 1024 lattice (2^30 spins), +-J couplings with p = 1/2 from
+seed 1, random initial spins and MT19937 streams from seed 2, quench at
+T = 0.9.  A step is one sweep (red pass + blue pass, every spin attempted once).
+psFlip = picoseconds per spin-flip attempt = step time / 2^30 (lower is better).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0.  Under torchrun (N > 1) every rank sweeps its
+own independent replica (same couplings, spin seed 2 + rank): the path has no
+exchange step at one lattice per GPU, so the ranks share nothing but the
+barrier and the max-over-ranks timing ("replicas only", weak scaling).
+`--impl reference` times the CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ps per spin-flip attempt (psFlip) at L=1024; batched vs plain psFlip"
+UNIT = "ps/attempt"
+
+# Roofline definitions (derivations in DESIGN.md, section "Roofline").
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+INT_LANES_PER_SM = 128                         # 4 SMSPs x 32 lanes, one 32-bit op each per clock
+ALU_PEAK_TOPS = SM_COUNT * INT_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12   # 40.27 Tops/s
+OPS_PER_ATTEMPT = {"mt19937": 17, "minstd": 11}  # algorithmic 32-bit integer ops per attempt
+BYTES_PER_ATTEMPT = 9 / 8                      # S_c read+write, S_c' once, 6 coupling bits
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=5)
+    p.add_argument("--plain-steps", type=int, default=300)
+    return p.parse_args()
+
+
+def workload_config(w):
+    return {"workload": "single lattice L=%d (%d spins), +-J p=1/2 seed_J=%d, random spins seed_spin=%d, "
+                        "%s streams, quench at T=%g" % (w.L, w.L ** 3, w.seed_J, w.seed_spin, w.kind.upper(), w.T),
+            "L": w.L, "rng": w.kind, "T": w.T, "seed_J": w.seed_J, "seed_spin": w.seed_spin,
+            "attempts_per_step": w.L ** 3,
+            "l2": "no flush: inputs (%d MiB of bit planes) exceed the 129 MB L2" % (w.L ** 3 * 4 // 8 // 2**20)}
+
+
+# ------------------------------------------------------------------ clocks ---
+class ClockSampler:
+    """nvidia-smi samples (every 50 ms) of SM clock and throttle reasons."""
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self, t0: float, t1: float) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.12)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = []
+        for line in self.file.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                frac = float("0." + parts[0].split(".")[1]) if "." in parts[0] else 0.0
+                rows.append((ts + frac, float(parts[1]), float(parts[2]), parts[5:9], parts[4]))
+            except (ValueError, IndexError):
+                continue
+        os.unlink(self.file.name)
+        inside = [r for r in rows if t0 - 0.05 <= r[0] <= t1 + 0.05]
+        note = "samples inside the timed region"
+        if not inside and rows:  # region shorter than the sampling period: nearest samples
+            inside = sorted(rows, key=lambda r: min(abs(r[0] - t0), abs(r[0] - t1)))[:3]
+            note = "timed region shorter than the sampling period: nearest samples"
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in inside for k in range(4) if r[3][k].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": reasons, "samples": len(inside), "note": note}
+
+
+# ----------------------------------------------------------- distributed ---
+class Dist:
+    def __init__(self, backend: str):
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float, device=None) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ------------------------------------------------------------ our kernels ---
+def traffic_from_profile(kind: str):
+    """DRAM bytes per flip-kernel launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "flip_L1024_%s.md" % kind)
+    src = os.path.join(ROOT, "paper_1411_0127_gb300", "csrc")
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(src)):
+        if name.startswith("isg_flip") or name == "isg_common.cuh":
+            h.update(open(os.path.join(src, name), "rb").read())
+    digest = h.hexdigest()[:16]
+    fields = {}
+    for line in open(path):
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            fields[k.strip()] = v.strip()
+    if fields.get("kernel_source_sha256_16") != digest:
+        return None
+    try:
+        return float(fields["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def cpu_baseline(w, target_s: float = 12.0) -> dict:
+    """The oracle, as it stands, on this host's cores: colour-pass pairs over a
+    block of streams of the same lattice, repeated for about target_s seconds."""
+    import oracle
+    threads = os.cpu_count() or 1
+    o = oracle.OracleSim(w.L, w.seed_J, w.seed_spin, w.beta, oracle.RNG_MT19937 if w.kind == "mt19937" else 0)
+    S, R = oracle.num_streams(w.L), oracle.rows_per_stream(w.L)
+    m = min(S, 4 * threads)
+    attempts_per_stream_pass = R * w.L // 2
+    t_start = time.perf_counter()
+    attempts = 0
+    t0 = 0
+    while time.perf_counter() - t_start < target_s:
+        o.pass_range(0, t0, t0 + m, threads)
+        o.pass_range(1, t0, t0 + m, threads)
+        attempts += 2 * m * attempts_per_stream_pass
+        t0 = (t0 + m) % S
+    dt = time.perf_counter() - t_start
+    o.close()
+    return {"value": dt * 1e12 / attempts, "unit": UNIT, "cores": min(threads, m), "kind": "oracle",
+            "sample": "red+blue passes over blocks of %d of the %d streams of the L=%d lattice (%d attempts, "
+                      "%.1f s wall)" % (m, S, w.L, attempts, dt)}
+
+
+def run_ours(a, dist: Dist):
+    import numpy as np
+    import torch
+    import paper_1411_0127_gb300 as isg
+    from paper_1411_0127_gb300 import workloads
+
+    torch.cuda.set_device(dist.local)
+    isg.use_torch_allocator()
+    w = workloads.LARGE
+    seed_spin = w.seed_spin + 1000 * dist.rank
+    sim = isg.Sim(w.L, w.seed_J, seed_spin, w.beta, w.kind)
+    stream = torch.cuda.current_stream()
+    N = w.L ** 3
+
+    sim.sweep(a.warmup, stream)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dist.local)
+    clocks.start()
+    time.sleep(0.2)
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h0 = time.time()
+    e0.record(stream)
+    for _ in range(a.steps):
+        sim.sweep(1, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    h1 = time.time()
+    dist.barrier()
+    clk = clocks.stop(h0, h1)
+    ms = e0.elapsed_time(e1)
+    ms_max = dist.max(ms, device="cuda")
+    launches = 2 * a.steps
+    launch_s = ms / 1e3 / launches
+    attempts_per_launch = N // 2
+    value = ms_max * 1e9 / (a.steps * N * dist.world)   # ps per attempt, whole job
+
+    # the plain per-colour kernel on the same lattice
+    plain = None
+    if a.plain_steps > 0:
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(a.plain_steps):
+            sim.sweep_plain(1, stream)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        plain = p0.elapsed_time(p1) * 1e9 / (a.plain_steps * N)
+
+    # end to end through the C-ABI with host buffers: pinned int8 spins in,
+    # one sweep, spins and the tracked energy out, every step
+    h_in = torch.empty(N, dtype=torch.int8, pin_memory=True).numpy()
+    h_out = torch.empty(N, dtype=torch.int8, pin_memory=True).numpy()
+    h_in[:] = sim.read_spins(stream)
+    n_e2e = max(1, min(a.e2e_steps, a.steps))
+    dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        sim.write_spins(h_in, stream)
+        sim.sweep(1, stream)
+        h_out[:] = sim.read_spins(stream)
+        sim.tracked_energy()
+    torch.cuda.synchronize()
+    e2e_s = dist.max(time.perf_counter() - t0, device="cuda")
+    e2e_value = e2e_s * 1e12 / (n_e2e * N * dist.world)
+
+    ops = OPS_PER_ATTEMPT[w.kind]
+    achieved_tops = ops * attempts_per_launch / launch_s / 1e12
+    hbm_gbs = BYTES_PER_ATTEMPT * attempts_per_launch / launch_s / 1e9
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm_peak, hbm_src = 6800.0, "fallback"
+    if os.path.exists(peaks_path):
+        try:
+            hbm_peak, hbm_src = float(json.load(open(peaks_path))["hbm_gbs"]), "measured"
+        except (ValueError, KeyError):
+            pass
+    traffic = traffic_from_profile(w.kind)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic", "impl": "ours",
+        "config": {**workload_config(w), "parallelism": "replicas only (one lattice per GPU)"},
+        "plain_psflip": plain,
+        "batched_psflip": None,
+        "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
+                     "frac": achieved_tops / ALU_PEAK_TOPS, "traffic": traffic,
+                     "kernel": "flip (one colour pass)", "ops_per_attempt": ops,
+                     "attempts_per_launch": attempts_per_launch, "launch_ms": launch_s * 1e3,
+                     "peak_source": "derived: 152 SMs x 128 lanes x 2070 MHz",
+                     "hbm": {"achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_gbs / hbm_peak,
+                             "peak_source": hbm_src, "bytes_per_attempt": BYTES_PER_ATTEMPT}},
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": N, "d2h_bytes_per_step": N + 8,
+                "steps": n_e2e,
+                "path": "isg_write_spins(pinned int8) + isg_sweep + isg_read_spins(pinned int8) + "
+                        "isg_tracked_energy"},
+        "gpu_launches": launches,
+    }
+    sim.close()
+    if dist.rank == 0 and dist.world == 1 and not a.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w)
+    return out
+
+
+# ----------------------------------------------------------- reference arm ---
+def run_reference(a, dist: Dist):
+    """The CPU oracle as it stands, on the host cores, on bounded samples of the
+    same workload; every step is one red and one blue pass over a block of
+    streams sized so that the whole run ends within about a minute."""
+    if dist.rank != 0:
+        return None
+    import oracle
+    from paper_1411_0127_gb300 import workloads
+    w = workloads.LARGE
+    threads = os.cpu_count() or 1
+    o = oracle.OracleSim(w.L, w.seed_J, w.seed_spin, w.beta, oracle.RNG_MT19937)
+    S, R = oracle.num_streams(w.L), oracle.rows_per_stream(w.L)
+    per_stream = R * w.L // 2
+    t = time.perf_counter()
+    o.pass_range(0, 0, threads, threads)
+    o.pass_range(1, 0, threads, threads)
+    cal = (time.perf_counter() - t) / threads            # seconds per stream pair, all cores busy
+    budget = 60.0 / max(1, a.steps + a.warmup)
+    m = int(max(threads, min(S, budget / max(cal, 1e-9))))
+    m = max(threads, m // threads * threads)
+    t0 = threads
+    for _ in range(a.warmup):
+        o.pass_range(0, t0 % S, t0 % S + m, threads)
+        o.pass_range(1, t0 % S, t0 % S + m, threads)
+        t0 += m
+    times = []
+    for _ in range(a.steps):
+        s = time.perf_counter()
+        o.pass_range(0, t0 % S, t0 % S + m, threads)
+        o.pass_range(1, t0 % S, t0 % S + m, threads)
+        times.append(time.perf_counter() - s)
+        t0 += m
+    attempts = 2 * m * per_stream
+    total = sum(times)
+    value = total * 1e12 / (attempts * a.steps)
+    o.close()
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": total * 1e3 / a.steps, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int8", "data": "synthetic", "impl": "reference",
+        "config": {**workload_config(w), "parallelism": "host threads over streams"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": min(threads, m), "kind": "oracle",
+                         "sample": "each step: red+blue passes over %d of the %d streams of the L=%d lattice "
+                                   "(%d attempts)" % (m, S, w.L, attempts)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    a = parse()
+    dist = Dist("nccl" if a.impl == "ours" else "gloo")
+    try:
+        out = run_reference(a, dist) if a.impl == "reference" else run_ours(a, dist)
+        if out is not None and dist.rank == 0:
+            print(json.dumps(out), flush=True)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -72,6 +72,7 @@ def lib() -> ctypes.CDLL:
             "or_move_counts": (None, [vp, vp, vp]),
             "or_acceptance_trial": (None, [i32, u32, dbl, i64, vp]),
             "or_peek_draws": (None, [vp, i64, i64, vp]),
+            "or_pass_range": (None, [vp, i32, i64, i64, i32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -152,6 +153,10 @@ class OracleSim:
 
     def sweep(self, n: int = 1, threads: int = 1):
         lib().or_sweep(self._h, n, threads)
+
+    def pass_range(self, colour: int, t0: int, t1: int, threads: int = 1):
+        """One colour pass over streams [t0, t1) only (timing samples)."""
+        lib().or_pass_range(self._h, colour, t0, t1, threads)
 
     def energy(self) -> int:
         return int(lib().or_energy(self._h))

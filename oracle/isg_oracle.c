@@ -308,6 +308,34 @@ static void colour_pass(or_sim *o, int c, int nthreads)
     free(jobs);
 }
 
+void or_pass_range(or_sim *o, int c, int64_t t0, int64_t t1, int nthreads)
+{
+    if (t0 < 0) t0 = 0;
+    if (t1 > o->S) t1 = o->S;
+    if (t1 <= t0) return;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > t1 - t0) nthreads = (int)(t1 - t0);
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    pass_job *jobs = (pass_job *)malloc(sizeof(pass_job) * (size_t)nthreads);
+    for (int k = 0; k < nthreads; ++k) {
+        jobs[k].o = o;
+        jobs[k].c = c;
+        jobs[k].t0 = t0 + (t1 - t0) * k / nthreads;
+        jobs[k].t1 = t0 + (t1 - t0) * (k + 1) / nthreads;
+        if (pthread_create(&th[k], NULL, pass_worker, &jobs[k]) != 0) { pass_worker(&jobs[k]); th[k] = 0; }
+    }
+    for (int k = 0; k < nthreads; ++k) {
+        if (th[k]) pthread_join(th[k], NULL);
+        o->dE += jobs[k].dE;
+        for (int u = 0; u < 7; ++u) {
+            o->attempts[u] += jobs[k].att[u];
+            o->accepts[u] += jobs[k].acc[u];
+        }
+    }
+    free(th);
+    free(jobs);
+}
+
 void or_sweep(or_sim *o, int64_t n, int nthreads)
 {
     for (int64_t k = 0; k < n; ++k) {

@@ -59,6 +59,9 @@ void    or_destroy(or_sim *s);
 /* n full sweeps (red then blue) using up to nthreads threads; the result does
  * not depend on nthreads. */
 void    or_sweep(or_sim *s, int64_t n, int nthreads);
+/* One colour pass (c = 0 red, 1 blue) over streams [t0, t1) only: a bounded
+ * sample of a sweep, used to time the oracle on large lattices. */
+void    or_pass_range(or_sim *s, int c, int64_t t0, int64_t t1, int nthreads);
 int64_t or_energy(const or_sim *s);           /* from scratch, Eq. (1) */
 int64_t or_tracked_energy(const or_sim *s);   /* initial energy + sum of accepted dE */
 int64_t or_overlap(const or_sim *a, const or_sim *b);  /* sum_i s^a_i s^b_i */

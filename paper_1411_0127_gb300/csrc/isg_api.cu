@@ -212,7 +212,15 @@ int isg_sweep_plain(isg_sim* h, int64_t n, void* stream) {
 
 int isg_sweep(isg_sim* h, int64_t n, void* stream) {
     if (!h || n < 0) { set_error("isg_sweep: bad handle or n"); return ISG_ERR_ARG; }
-    return isg_sweep_plain(h, n, stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int64_t k = 0; k < n; ++k) {
+        cudaError_t e = launch_flip_fast(h, 0, s);
+        if (e == cudaSuccess) e = launch_flip_fast(h, 1, s);
+        if (e != cudaSuccess) return cuda_fail(e, "flip kernel launch");
+    }
+    h->sweeps += n;
+    h->last_stream = s;
+    return ISG_OK;
 }
 
 int isg_sweeps_done(const isg_sim* h, int64_t* n) {

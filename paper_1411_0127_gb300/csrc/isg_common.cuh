@@ -87,6 +87,19 @@ struct MinstdTable {
 };
 MinstdTable minstd_table();
 
+// Arguments of one colour pass of the flip kernels.
+struct FlipArgs {
+    unsigned char* planes;
+    int64_t plane_bytes;
+    int L, half, W, nt, c;
+    int64_t R, S, rows;
+    uint32_t thr1, thr2, thr3;
+    uint32_t* rng;
+    uint32_t* rng_pos;
+    long long* dE;
+    MinstdTable mt;
+};
+
 // One warp-wide step of a MINSTD stream: lane j holds x_{n+j+1}; returns the
 // draw 2*x and moves every lane forward by nvalid positions (a32 = 16807^32).
 __device__ __forceinline__ uint32_t minstd_warp_step(uint32_t& x, uint32_t a32, int nvalid, int lane) {
@@ -184,7 +197,8 @@ struct isg_sim {
     unsigned char* planes = nullptr;    // 8 planes: index 4*c + q, q = S, Jx, Jy, Jz
     uint32_t* rng = nullptr;            // MT: S * 624 ring words; MINSTD: S states
     uint32_t* rng_pos = nullptr;        // MT: S ring positions
-    long long* scal = nullptr;          // [0] tracked dE, [1] scratch sum, [2] hash
+    long long* scal = nullptr;          // [0] tracked dE, [1] scratch sum, [2] hash, [3] stream tickets
+    unsigned long long tickets = 0;     // value of the stream-ticket counter before the next launch
     int64_t E0 = 0;                     // energy when tracking (re)started
     int64_t sweeps = 0;
     cudaStream_t last_stream = nullptr;
@@ -205,7 +219,9 @@ void dev_free(isg_sim* h, void* p);
 // kernels (launchers) implemented in the .cu files
 cudaError_t launch_init_planes(isg_sim* h, cudaStream_t s);
 cudaError_t launch_init_rng(isg_sim* h, cudaStream_t s);
+FlipArgs make_flip_args(isg_sim* h, int colour);
 cudaError_t launch_flip_plain(isg_sim* h, int colour, cudaStream_t s);
+cudaError_t launch_flip_fast(isg_sim* h, int colour, cudaStream_t s);
 cudaError_t launch_energy(const isg_sim* h, long long* out, cudaStream_t s);
 cudaError_t launch_overlap(const isg_sim* a, const isg_sim* b, long long* out, cudaStream_t s);
 cudaError_t launch_hash(const isg_sim* h, unsigned long long* out, cudaStream_t s);

@@ -19,18 +19,6 @@ namespace isg {
 
 constexpr int kFlipWarps = 4;
 
-struct FlipArgs {
-    unsigned char* planes;
-    int64_t plane_bytes;
-    int L, half, W, nt, c;
-    int64_t R, S, rows;
-    uint32_t thr1, thr2, thr3;
-    uint32_t* rng;
-    uint32_t* rng_pos;
-    long long* dE;
-    MinstdTable mt;
-};
-
 template <int KIND>
 struct RingWords {
     static constexpr int value = (KIND == ISG_RNG_MT19937) ? kMtN : 0;
@@ -165,7 +153,7 @@ MinstdTable minstd_table() {
     return t;
 }
 
-static FlipArgs make_args(isg_sim* h, int colour) {
+FlipArgs make_flip_args(isg_sim* h, int colour) {
     FlipArgs a;
     a.planes = h->planes;
     a.plane_bytes = h->plane_bytes;
@@ -189,7 +177,7 @@ static FlipArgs make_args(isg_sim* h, int colour) {
 
 template <typename Word, int KIND>
 static cudaError_t launch_plain_t(isg_sim* h, int colour, cudaStream_t s) {
-    const FlipArgs a = make_args(h, colour);
+    const FlipArgs a = make_flip_args(h, colour);
     const int blocks = (int)((h->S + kFlipWarps - 1) / kFlipWarps);
     const size_t smem = (size_t)kFlipWarps * (RingWords<KIND>::value + 3 * kCondWords) * sizeof(uint32_t);
     flip_plain_kernel<Word, KIND><<<blocks, kFlipWarps * 32, smem, s>>>(a);

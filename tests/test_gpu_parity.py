@@ -178,6 +178,19 @@ def test_plain_and_default_sweep_agree(isg):
     assert a.hash() == b.hash() and a.tracked_energy() == b.tracked_energy()
 
 
+@pytest.mark.parametrize("kind", ["minstd", "mt19937"])
+@pytest.mark.parametrize("L", [6, 48, 98, 256])
+def test_fast_and_plain_kernels_interleaved(isg, L, kind):
+    """The two flip kernels share the stream-state format: alternating them on
+    one handle follows the oracle's trajectory."""
+    g, o = pair(isg, L, kind, 1 / 0.9, seed_J=7, seed_spin=8)
+    for k in range(6):
+        (g.sweep if k % 2 == 0 else g.sweep_plain)(1)
+        o.sweep(1, threads=8)
+        assert g.tracked_energy() == o.tracked_energy(), k
+    assert np.array_equal(g.read_spins(), o.spins())
+
+
 def test_gauge_transform_on_gpu(isg):
     L = 24
     rng = np.random.default_rng(5)
