@@ -20,10 +20,36 @@ namespace isg {
 
 constexpr int kFastWarps = 4;
 
-// MT19937 twist of one word: x_{k+624} from x_k, x_{k+1}, x_{k+397}.
-__device__ __forceinline__ uint32_t mt_twist(uint32_t a, uint32_t b, uint32_t m) {
+// Multipliers that turn the generator's shifts into integer multiplies:
+// v >> k == umulhi(v, 2^(32-k)) and v << k == v * 2^k (mod 2^32), exactly.
+// They arrive as kernel arguments so that the compiler cannot fold them back
+// into shift instructions: the multiplies run on the FMA pipe, leaving only the
+// XORs on the (half-rate) logic pipe.
+struct MtMul {
+    uint32_t hi31;  // 2^31: >> 1
+    uint32_t hi21;  // 2^21: >> 11
+    uint32_t hi14;  // 2^14: >> 18
+    uint32_t lo7;   // 2^7:  << 7
+    uint32_t lo15;  // 2^15: << 15
+};
+
+// MT19937 twist of one word: x_{k+624} from x_k, x_{k+1}, x_{k+397}.  The odd
+// test uses b - 2 (b >> 1) = b & 1.
+__device__ __forceinline__ uint32_t mt_twist(uint32_t a, uint32_t b, uint32_t m, const MtMul& k) {
     const uint32_t y = (a & 0x80000000u) | (b & 0x7FFFFFFFu);
-    return m ^ (y >> 1) ^ ((0u - (b & 1u)) & 0x9908B0DFu);
+    const uint32_t ys = __umulhi(y, k.hi31);
+    const uint32_t bh = __umulhi(b, k.hi31);
+    const uint32_t odd = b - 2u * bh;
+    return m ^ ys ^ (odd * 0x9908B0DFu);
+}
+
+// MT19937 tempering with the shifts done as multiplies (see MtMul).
+__device__ __forceinline__ uint32_t mt_temper_mul(uint32_t v, const MtMul& k) {
+    v ^= __umulhi(v, k.hi21);
+    v ^= (v * k.lo7) & 0x9D2C5680u;
+    v ^= (v * k.lo15) & 0xEFC60000u;
+    v ^= __umulhi(v, k.hi14);
+    return v;
 }
 
 // Two 32-draw blocks of an MT19937 stream held in a mirrored 1248-word ring.
@@ -31,14 +57,14 @@ __device__ __forceinline__ uint32_t mt_twist(uint32_t a, uint32_t b, uint32_t m)
 // points 64 draws further.  Reads of both blocks precede all writes (one warp
 // barrier between): block B's inputs x_{k+32+l+397} were written 195 or more
 // draws earlier, and the words both blocks overwrite are read first.
-__device__ __forceinline__ void mt_pair(uint32_t* ring, int& iA, uint32_t& dA, uint32_t& dB) {
+__device__ __forceinline__ void mt_pair(uint32_t* ring, int& iA, uint32_t& dA, uint32_t& dB, const MtMul& k) {
     int iB = iA + 32;
     iB = iB >= kMtN ? iB - kMtN : iB;
     const uint32_t aA = ring[iA], bA = ring[iA + 1], mA = ring[iA + kMtM];
     const uint32_t aB = ring[iB], bB = ring[iB + 1], mB = ring[iB + kMtM];
     __syncwarp();
-    const uint32_t vA = mt_twist(aA, bA, mA);
-    const uint32_t vB = mt_twist(aB, bB, mB);
+    const uint32_t vA = mt_twist(aA, bA, mA, k);
+    const uint32_t vB = mt_twist(aB, bB, mB, k);
     ring[iA] = vA;
     ring[iA + kMtN] = vA;
     ring[iB] = vB;
@@ -46,15 +72,15 @@ __device__ __forceinline__ void mt_pair(uint32_t* ring, int& iA, uint32_t& dA, u
     __syncwarp();
     iA = iB + 32;
     iA = iA >= kMtN ? iA - kMtN : iA;
-    dA = mt_temper(vA);
-    dB = mt_temper(vB);
+    dA = mt_temper_mul(vA, k);
+    dB = mt_temper_mul(vB, k);
 }
 
 // One block of up to 32 draws (tail of a row group); lanes >= nvalid consume nothing.
-__device__ __forceinline__ uint32_t mt_single(uint32_t* ring, int& iA, int lane, int nvalid) {
+__device__ __forceinline__ uint32_t mt_single(uint32_t* ring, int& iA, int lane, int nvalid, const MtMul& k) {
     const uint32_t a = ring[iA], b = ring[iA + 1], m = ring[iA + kMtM];
     __syncwarp();
-    const uint32_t v = mt_twist(a, b, m);
+    const uint32_t v = mt_twist(a, b, m, k);
     if (lane < nvalid) {
         ring[iA] = v;
         ring[iA + kMtN] = v;
@@ -62,7 +88,7 @@ __device__ __forceinline__ uint32_t mt_single(uint32_t* ring, int& iA, int lane,
     __syncwarp();
     iA += nvalid;
     iA = iA >= kMtN ? iA - kMtN : iA;
-    return mt_temper(v);
+    return mt_temper_mul(v, k);
 }
 
 // Logic phase for one word of colour c at row r = y + L z, word k (see the
@@ -122,6 +148,7 @@ struct FastExtra {
     unsigned long long base;      // its value when this launch starts
     uint32_t c1, c2, c3;          // compared thresholds (MT: thr; MINSTD: ceil(thr/2))
     uint32_t a64;                 // 16807^64 mod (2^31 - 1)
+    MtMul mul;
 };
 
 template <typename Word, int KIND>
@@ -174,7 +201,7 @@ __global__ void __launch_bounds__(kFastWarps * 32, 8) flip_fast_kernel(FlipArgs 
             for (int q = 0; q < npairs; ++q) {
                 uint32_t dA, dB;
                 if (kMT) {
-                    mt_pair(ring, iA, dA, dB);
+                    mt_pair(ring, iA, dA, dB, x.mul);
                 } else {
                     dA = xA;
                     dB = xB;
@@ -196,7 +223,7 @@ __global__ void __launch_bounds__(kFastWarps * 32, 8) flip_fast_kernel(FlipArgs 
                 const int nvalid = rem < 32 ? rem : 32;
                 uint32_t d;
                 if (kMT) {
-                    d = mt_single(ring, iA, lane, nvalid);
+                    d = mt_single(ring, iA, lane, nvalid, x.mul);
                 } else {
                     d = xA;
                     const int src = lane + nvalid;
@@ -257,6 +284,11 @@ static cudaError_t launch_fast_t(isg_sim* h, int colour, cudaStream_t s) {
         x.c3 = (uint32_t)(((uint64_t)h->thr[3] + 1) / 2);
     }
     x.a64 = minstd_mulmod(a.mt.pow[32], a.mt.pow[32]);
+    x.mul.hi31 = 1u << 31;
+    x.mul.hi21 = 1u << 21;
+    x.mul.hi14 = 1u << 14;
+    x.mul.lo7 = 1u << 7;
+    x.mul.lo15 = 1u << 15;
     constexpr int kRing = KIND == ISG_RNG_MT19937 ? 2 * kMtN : 0;
     const size_t smem = (size_t)kFastWarps * (kRing + 3 * kCondWords) * sizeof(uint32_t);
     static int sms = 0;
