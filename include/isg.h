@@ -143,6 +143,27 @@ int isg_save(const isg_sim *h, void *host_buf, size_t *n, void *cuda_stream);
  * same trajectory, bit for bit, as continuing the saved one. */
 int isg_load(const void *host_buf, size_t n, isg_sim **out);
 
+/* ------------------------------------------------------- no allocation --- */
+
+/* The energy of Eq. 1, like isg_energy, for callers that must not allocate
+ * device memory when they ask for it: code that enqueues work while a stream
+ * is being captured into a CUDA graph (where cudaMalloc is not allowed),
+ * real-time loops that cannot take the device-wide synchronisation an
+ * allocation may cause, and processes that work inside a device-memory budget
+ * fixed up front.  The paper has no counterpart to this call; it exists only
+ * for those callers.
+ *
+ * Async: enqueues two kernels on cuda_stream and writes E (int64) to the
+ * caller's device pointer dev_E; it calls no cudaMalloc, cudaFree or other
+ * allocating routine.  Its partial sums live in a fixed array of 8192 int64
+ * (64 KiB) compiled into the library, held by every device that loads it until
+ * the process exits.  Lattices needing more partial sums (L > 1448) give
+ * ISG_ERR_ARG.  All calls share that array: calls whose kernels overlap on the
+ * GPU (e.g. on two streams) race and give wrong results.  The first call on
+ * each device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture begins. */
+int isg_energy_static_scratch(const isg_sim *h, long long *dev_E, void *cuda_stream);
+
 /* ------------------------------------------------------------- testing --- */
 
 /* Run the device flip rule on n stencils (sync).  code[j] bits: 0 = spin bit,

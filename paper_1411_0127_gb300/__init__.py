@@ -49,6 +49,7 @@ SIGNATURES = {
     "isg_load": (_i32, [_vp, _sz, _PP]),
     "isg_stencil_decisions": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp]),
     "isg_peek_draws": (_i32, [_vp, _i64, _i64, _vp]),
+    "isg_energy_static_scratch": (_i32, [_vp, _vp, _vp]),
 }
 
 
