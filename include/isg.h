@@ -50,6 +50,7 @@ enum {
 enum { ISG_RNG_MINSTD = 0, ISG_RNG_MT19937 = 1 };
 
 typedef struct isg_sim isg_sim;
+typedef struct isg_batch isg_batch;
 
 /* ---------------------------------------------------------------- setup --- */
 
@@ -142,6 +143,45 @@ int isg_save(const isg_sim *h, void *host_buf, size_t *n, void *cuda_stream);
  * truncated buffer gives ISG_ERR_ARG.  Continuing the loaded handle gives the
  * same trajectory, bit for bit, as continuing the saved one. */
 int isg_load(const void *host_buf, size_t n, isg_sim **out);
+
+/* --------------------------------------------------------------- batch --- */
+
+/* Many disorder samples swept together, as the paper fills the GPU with many
+ * coded samples (Sec. 2, samples k; Sec. 4 results against k).  Sample s has
+ * size L[s] (even, 4..2048), couplings from seed_J[s], inverse temperature
+ * beta[s] > 0, and two replicas whose spins and streams come from seed_spin[2s]
+ * and seed_spin[2s+1]; all samples use rng_kind.  Every replica follows exactly
+ * the trajectory of a lone isg_create handle with the same arguments.
+ * Sync; ISG_ERR_ARG on a bad size, beta or kind (nothing allocated). */
+int isg_batch_create(int n, const int *L, const uint64_t *seed_J, const uint64_t *seed_spin,
+                     const double *beta, int rng_kind, isg_batch **out);
+
+/* Free the batch and all its replicas (NULL is ignored). */
+void isg_batch_destroy(isg_batch *b);
+
+/* Number of samples, of work bundles (streams of small lattices packed 32 per
+ * bundle) and of spin-flip attempts per sweep of the whole batch. */
+int isg_batch_info(const isg_batch *b, int *samples, int *bundles, int64_t *attempts_per_sweep);
+
+/* Handle of replica i (0 <= i < 2n; replicas 2s, 2s+1 belong to sample s).  The
+ * handle stays owned by the batch: use it with the measuring, reading and
+ * checkpoint calls, never with isg_destroy. */
+int isg_batch_member(isg_batch *b, int i, isg_sim **out);
+
+/* Enqueue `sweeps` sweeps of every replica (async).  The work runs as persistent
+ * launches of group_sweeps sweeps (<= 0 picks 64): one CTA per SM takes bundle
+ * after bundle; the group launch is captured once into a CUDA graph and
+ * replayed; a remainder of sweeps % group_sweeps is launched directly. */
+int isg_batch_run(isg_batch *b, int64_t sweeps, int group_sweeps, void *cuda_stream);
+
+/* Energies from scratch of the 2n replicas (E[2s], E[2s+1]) and overlaps
+ * Q[s] = sum_i s^a_i s^b_i of the two replicas of each sample (sync).  Either
+ * pointer may be NULL. */
+int isg_batch_measure(isg_batch *b, int64_t *E, int64_t *Q, void *cuda_stream);
+
+/* Tracked energies (2n) and Zobrist hashes (2n) of the replicas (sync).  Either
+ * pointer may be NULL. */
+int isg_batch_tracked(isg_batch *b, int64_t *E, uint64_t *H, void *cuda_stream);
 
 /* ------------------------------------------------------- no allocation --- */
 

@@ -50,6 +50,13 @@ SIGNATURES = {
     "isg_stencil_decisions": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp]),
     "isg_peek_draws": (_i32, [_vp, _i64, _i64, _vp]),
     "isg_energy_static_scratch": (_i32, [_vp, _vp, _vp]),
+    "isg_batch_create": (_i32, [_i32, _vp, _vp, _vp, _vp, _i32, _PP]),
+    "isg_batch_destroy": (None, [_vp]),
+    "isg_batch_info": (_i32, [_vp, _vp, _vp, _vp]),
+    "isg_batch_member": (_i32, [_vp, _i32, _PP]),
+    "isg_batch_run": (_i32, [_vp, _i64, _i32, _vp]),
+    "isg_batch_measure": (_i32, [_vp, _vp, _vp, _vp]),
+    "isg_batch_tracked": (_i32, [_vp, _vp, _vp, _vp]),
 }
 
 
@@ -254,3 +261,70 @@ def stencil_decisions(codes: np.ndarray, draws: np.ndarray, thr) -> tuple[np.nda
     u = np.empty(codes.size, dtype=np.uint8)
     _check(lib().isg_stencil_decisions(_ptr(codes), _ptr(draws), codes.size, _ptr(t), _ptr(flip), _ptr(u)))
     return flip, u
+
+
+class _Member(Sim):
+    """A replica owned by a Batch (never destroyed through this object)."""
+
+    def close(self):
+        self._h = None
+
+
+class Batch:
+    """Many samples of uneven L, two replicas each, swept by persistent launches."""
+
+    def __init__(self, L, seed_J, seed_spin, beta, rng_kind="mt19937"):
+        kind = RNG_KINDS[rng_kind] if isinstance(rng_kind, str) else int(rng_kind)
+        n = len(L)
+        La = np.ascontiguousarray(L, dtype=np.int32)
+        J = np.ascontiguousarray([int(v) & (2**64 - 1) for v in seed_J], dtype=np.uint64)
+        S = np.ascontiguousarray([int(v) & (2**64 - 1) for v in seed_spin], dtype=np.uint64)
+        B = np.ascontiguousarray(beta, dtype=np.float64)
+        assert J.size == n and S.size == 2 * n and B.size == n
+        h = ctypes.c_void_p()
+        _check(lib().isg_batch_create(n, _ptr(La), _ptr(J), _ptr(S), _ptr(B), kind, ctypes.byref(h)))
+        self._h = h.value
+        self.n, self.kind = n, kind
+        self.L = [int(v) for v in La]
+        self.beta = [float(v) for v in B]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().isg_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        s, b, a = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+        _check(lib().isg_batch_info(self._h, ctypes.byref(s), ctypes.byref(b), ctypes.byref(a)))
+        return {"samples": s.value, "bundles": b.value, "attempts_per_sweep": a.value}
+
+    def run(self, sweeps: int, group_sweeps: int = 64, stream=None):
+        _check(lib().isg_batch_run(self._h, int(sweeps), int(group_sweeps), _stream(stream)))
+
+    def member(self, i: int) -> Sim:
+        h = ctypes.c_void_p()
+        _check(lib().isg_batch_member(self._h, int(i), ctypes.byref(h)))
+        m = _Member.__new__(_Member)
+        m._h = h.value
+        m.L = self.L[i // 2]
+        m.N = m.L ** 3
+        m.kind, m.beta = self.kind, self.beta[i // 2]
+        return m
+
+    def measure(self, stream=None):
+        E = np.empty(2 * self.n, dtype=np.int64)
+        Q = np.empty(self.n, dtype=np.int64)
+        _check(lib().isg_batch_measure(self._h, _ptr(E), _ptr(Q), _stream(stream)))
+        return E, Q
+
+    def tracked(self, stream=None):
+        E = np.empty(2 * self.n, dtype=np.int64)
+        H = np.empty(2 * self.n, dtype=np.uint64)
+        _check(lib().isg_batch_tracked(self._h, _ptr(E), _ptr(H), _stream(stream)))
+        return E, H

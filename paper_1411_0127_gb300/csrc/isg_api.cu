@@ -65,7 +65,7 @@ static bool beta_ok(double beta) { return beta > 0.0; }  // false for 0, negativ
 static int alloc_sim(isg_sim* h) {
     h->half = h->L / 2;
     const int w64 = (h->half + 63) / 64, w32 = (h->half + 31) / 32;
-    h->wbits = (2 * w64 == w32) ? 64 : 32;
+    h->wbits = (2 * w64 == w32 && !h->force32) ? 64 : 32;
     h->W = (h->half + h->wbits - 1) / h->wbits;
     h->nt = h->half - (h->W - 1) * h->wbits;
     h->rows = (int64_t)h->L * h->L;
@@ -132,6 +132,38 @@ static int restart_tracking(isg_sim* h, cudaStream_t s) {
     return e == cudaSuccess ? ISG_OK : cuda_fail(e, "reset tracked energy");
 }
 
+int create_sim(int L, uint64_t seed_J, uint64_t seed_spin, double beta, int rng_kind, bool force32,
+               isg_sim** out) {
+    if (!out) { set_error("isg_create: out is NULL"); return ISG_ERR_ARG; }
+    *out = nullptr;
+    if (L < 4 || L > 2048 || (L & 1)) { set_error("isg_create: L=%d must be even and in [4, 2048]", L); return ISG_ERR_ARG; }
+    if (!beta_ok(beta)) { set_error("isg_create: beta must be > 0 (got %g)", beta); return ISG_ERR_ARG; }
+    if (rng_kind != ISG_RNG_MINSTD && rng_kind != ISG_RNG_MT19937) {
+        set_error("isg_create: unknown rng_kind %d", rng_kind);
+        return ISG_ERR_ARG;
+    }
+    isg_sim* h = new_sim();
+    if (!h) { set_error("isg_create: out of host memory"); return ISG_ERR_NOMEM; }
+    h->L = L;
+    h->kind = rng_kind;
+    h->beta = beta;
+    h->seed_J = seed_J;
+    h->seed_spin = seed_spin;
+    h->force32 = force32;
+    thresholds(beta, h->thr);
+    int rc = alloc_sim(h);
+    if (rc) { free_sim(h); return rc; }
+    cudaError_t e = launch_init_planes(h, 0);
+    if (e == cudaSuccess) e = launch_init_rng(h, 0);
+    if (e != cudaSuccess) { free_sim(h); return cuda_fail(e, "init kernels"); }
+    rc = restart_tracking(h, 0);
+    if (rc) { free_sim(h); return rc; }
+    *out = h;
+    return ISG_OK;
+}
+
+void destroy_sim(isg_sim* h) { free_sim(h); }
+
 }  // namespace isg
 
 using namespace isg;
@@ -153,31 +185,7 @@ int isg_set_allocator(void* (*alloc)(size_t, void*), void (*free_fn)(void*, void
 }
 
 int isg_create(int L, uint64_t seed_J, uint64_t seed_spin, double beta, int rng_kind, isg_sim** out) {
-    if (!out) { set_error("isg_create: out is NULL"); return ISG_ERR_ARG; }
-    *out = nullptr;
-    if (L < 4 || L > 2048 || (L & 1)) { set_error("isg_create: L=%d must be even and in [4, 2048]", L); return ISG_ERR_ARG; }
-    if (!beta_ok(beta)) { set_error("isg_create: beta must be > 0 (got %g)", beta); return ISG_ERR_ARG; }
-    if (rng_kind != ISG_RNG_MINSTD && rng_kind != ISG_RNG_MT19937) {
-        set_error("isg_create: unknown rng_kind %d", rng_kind);
-        return ISG_ERR_ARG;
-    }
-    isg_sim* h = new_sim();
-    if (!h) { set_error("isg_create: out of host memory"); return ISG_ERR_NOMEM; }
-    h->L = L;
-    h->kind = rng_kind;
-    h->beta = beta;
-    h->seed_J = seed_J;
-    h->seed_spin = seed_spin;
-    thresholds(beta, h->thr);
-    int rc = alloc_sim(h);
-    if (rc) { free_sim(h); return rc; }
-    cudaError_t e = launch_init_planes(h, 0);
-    if (e == cudaSuccess) e = launch_init_rng(h, 0);
-    if (e != cudaSuccess) { free_sim(h); return cuda_fail(e, "init kernels"); }
-    rc = restart_tracking(h, 0);
-    if (rc) { free_sim(h); return rc; }
-    *out = h;
-    return ISG_OK;
+    return create_sim(L, seed_J, seed_spin, beta, rng_kind, false, out);
 }
 
 void isg_destroy(isg_sim* h) {
@@ -405,6 +413,7 @@ int isg_load(const void* buf, size_t n, isg_sim** out) {
     h->beta = hd.beta;
     h->seed_J = hd.seed_J;
     h->seed_spin = hd.seed_spin;
+    h->force32 = hd.wbits == 32;
     thresholds(h->beta, h->thr);
     int rc = alloc_sim(h);
     if (rc) { free_sim(h); return rc; }

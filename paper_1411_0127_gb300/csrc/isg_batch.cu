@@ -1,0 +1,341 @@
+// isg_batch.cu -- batched persistent engine: many disorder samples of uneven L,
+// two replicas each, swept by one persistent launch per group of sweeps.
+//
+// The paper fills the GPU with many samples at once (Sec. 2, coded samples k;
+// Sec. 4 results, psFlip against k).  Here a batch is a set of ordinary
+// lattices (32-bit words forced, so one kernel template serves every L), two
+// per sample with the same couplings and different spin seeds, and:
+//   * on the host their RNG streams are packed into bundles: a lattice with more
+//     than 32 streams is one bundle; smaller lattices are packed together, at
+//     most 32 streams per bundle;
+//   * one CTA of 32 warps per SM takes bundle after bundle (largest first) from
+//     a counter and runs all sweeps of the launch on it: warp w sweeps entries
+//     w, w + 32, ... of the bundle, and a block barrier separates the colour
+//     passes; no lattice spans two CTAs, so no grid-wide barrier is needed;
+//   * when a bundle has at most 32 streams each warp keeps its stream's MT19937
+//     words in shared memory for the whole launch;
+//   * the bundle counter returns to zero when the last CTA leaves, so the
+//     launch is captured once into a CUDA graph and replayed.
+// Every lattice follows exactly the trajectory it has alone (same map from
+// site to stream and draw), which the tests check against isg_sweep and the
+// CPU oracle.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "isg_stream.cuh"
+
+struct isg_batch {
+    int n = 0;                          // samples
+    int kind = 0;
+    std::vector<isg_sim*> reps;         // 2n lattices, replica-major
+    isg::FlipArgs* d_reps = nullptr;    // per-lattice descriptors
+    int2* d_entries = nullptr;          // (lattice, stream) grouped by bundle
+    int* d_boff = nullptr;              // bundle offsets into d_entries
+    unsigned* d_ctr = nullptr;          // [0] next bundle, [1] CTAs done
+    int nbundles = 0;
+    int64_t attempts_per_sweep = 0;
+    cudaStream_t cap = nullptr;         // private stream used for graph capture
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    int graph_group = 0;
+};
+
+namespace isg {
+
+constexpr int kBatchWarps = 32;
+
+struct BatchArgs {
+    const FlipArgs* reps;
+    const int2* entries;
+    const int* boff;
+    int nbundles;
+    int sweeps;
+    unsigned* ctr;
+};
+
+template <int KIND>
+__global__ void __launch_bounds__(kBatchWarps * 32, 1) batch_kernel(BatchArgs b, StreamConst k) {
+    extern __shared__ uint32_t smem[];
+    __shared__ int s_bundle;
+    constexpr int kRing = KIND == ISG_RNG_MT19937 ? 2 * kMtN : 0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t* ring = smem + wid * (kRing + 3 * kCondWords);
+    uint32_t* cond = ring + kRing;
+    for (;;) {
+        if (threadIdx.x == 0) s_bundle = (int)atomicAdd(&b.ctr[0], 1u);
+        __syncthreads();
+        const int bid = s_bundle;
+        __syncthreads();
+        if (bid >= b.nbundles) break;
+        const int e0 = b.boff[bid], n = b.boff[bid + 1] - e0;
+        const bool resident = n <= kBatchWarps;
+        StreamRegs st;
+        if (resident && wid < n) {
+            const int2 e = b.entries[e0 + wid];
+            load_stream<KIND>(b.reps[e.x], e.y, ring, st, k, lane);
+        }
+        for (int pass = 0; pass < 2 * b.sweeps; ++pass) {
+            for (int j = wid; j < n; j += kBatchWarps) {
+                const int2 e = b.entries[e0 + j];
+                const FlipArgs& a = b.reps[e.x];
+                if (!resident) load_stream<KIND>(a, e.y, ring, st, k, lane);
+                int dE = 0;
+                stream_pass<uint32_t, KIND>(a, pass & 1, e.y, ring, cond, st, k, lane, dE);
+                if (!resident) store_stream<KIND>(a, e.y, ring, st, lane);
+                for (int sh = 16; sh; sh >>= 1) dE += __shfl_xor_sync(kFull, dE, sh);
+                if (lane == 0 && dE != 0) atomicAdd((unsigned long long*)a.dE, (unsigned long long)(long long)dE);
+            }
+            __syncthreads();
+        }
+        if (resident && wid < n) {
+            const int2 e = b.entries[e0 + wid];
+            store_stream<KIND>(b.reps[e.x], e.y, ring, st, lane);
+        }
+    }
+    // the last CTA to leave returns both counters to zero for the next launch
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned done = atomicAdd(&b.ctr[1], 1u);
+        if (done == gridDim.x - 1) {
+            atomicExch(&b.ctr[0], 0u);
+            atomicExch(&b.ctr[1], 0u);
+            __threadfence();
+        }
+    }
+}
+
+static size_t batch_smem(int kind) {
+    const int ring = kind == ISG_RNG_MT19937 ? 2 * kMtN : 0;
+    return (size_t)kBatchWarps * (ring + 3 * kCondWords) * sizeof(uint32_t);
+}
+
+static int batch_grid(const isg_batch* b) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return std::max(1, std::min(sms, b->nbundles));
+}
+
+static cudaError_t batch_launch(isg_batch* b, int sweeps, cudaStream_t s) {
+    BatchArgs a;
+    a.reps = b->d_reps;
+    a.entries = b->d_entries;
+    a.boff = b->d_boff;
+    a.nbundles = b->nbundles;
+    a.sweeps = sweeps;
+    a.ctr = b->d_ctr;
+    const StreamConst k = stream_const();
+    const size_t smem = batch_smem(b->kind);
+    const int grid = batch_grid(b);
+    if (b->kind == ISG_RNG_MT19937)
+        batch_kernel<ISG_RNG_MT19937><<<grid, kBatchWarps * 32, smem, s>>>(a, k);
+    else
+        batch_kernel<ISG_RNG_MINSTD><<<grid, kBatchWarps * 32, smem, s>>>(a, k);
+    return cudaGetLastError();
+}
+
+static void batch_free(isg_batch* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (!b->reps.empty() && b->reps[0]) {
+        dev_free(b->reps[0], b->d_reps);
+        dev_free(b->reps[0], b->d_entries);
+        dev_free(b->reps[0], b->d_boff);
+        dev_free(b->reps[0], b->d_ctr);
+    }
+    for (isg_sim* h : b->reps) destroy_sim(h);
+    delete b;
+}
+
+}  // namespace isg
+
+using namespace isg;
+
+extern "C" {
+
+int isg_batch_create(int n, const int* L, const uint64_t* seed_J, const uint64_t* seed_spin, const double* beta,
+                     int rng_kind, isg_batch** out) {
+    if (!out) { set_error("isg_batch_create: out is NULL"); return ISG_ERR_ARG; }
+    *out = nullptr;
+    if (n < 1 || !L || !seed_J || !seed_spin || !beta) { set_error("isg_batch_create: bad argument"); return ISG_ERR_ARG; }
+    if (rng_kind != ISG_RNG_MINSTD && rng_kind != ISG_RNG_MT19937) {
+        set_error("isg_batch_create: unknown rng_kind %d", rng_kind);
+        return ISG_ERR_ARG;
+    }
+    for (int s = 0; s < n; ++s)
+        if (L[s] < 4 || L[s] > 2048 || (L[s] & 1) || !(beta[s] > 0.0)) {
+            set_error("isg_batch_create: sample %d has L=%d beta=%g", s, L[s], beta[s]);
+            return ISG_ERR_ARG;
+        }
+    isg_batch* b = new (std::nothrow) isg_batch();
+    if (!b) { set_error("isg_batch_create: out of host memory"); return ISG_ERR_NOMEM; }
+    b->n = n;
+    b->kind = rng_kind;
+    b->reps.assign(2 * n, nullptr);
+    for (int r = 0; r < 2 * n; ++r) {
+        const int s = r / 2;
+        const int rc = create_sim(L[s], seed_J[s], seed_spin[r], beta[s], rng_kind, true, &b->reps[r]);
+        if (rc) { batch_free(b); return rc; }
+        b->attempts_per_sweep += (int64_t)L[s] * L[s] * L[s];
+    }
+
+    // bundles: big lattices alone, small ones first-fit into 32 entries
+    struct Bundle {
+        std::vector<int2> e;
+        double work;
+    };
+    std::vector<Bundle> bundles;
+    std::vector<int> small;
+    for (int r = 0; r < 2 * n; ++r) {
+        const isg_sim* h = b->reps[r];
+        if (h->S > kBatchWarps) {
+            Bundle bd;
+            for (int64_t t = 0; t < h->S; ++t) bd.e.push_back(make_int2(r, (int)t));
+            bd.work = (double)((h->S + kBatchWarps - 1) / kBatchWarps) * (double)h->R * h->half;
+            bundles.push_back(bd);
+        } else {
+            small.push_back(r);
+        }
+    }
+    std::stable_sort(small.begin(), small.end(), [&](int x, int y) {
+        const isg_sim *a = b->reps[x], *c = b->reps[y];
+        if (a->S != c->S) return a->S > c->S;
+        return a->L > c->L;
+    });
+    std::vector<Bundle> packs;
+    for (int r : small) {
+        const isg_sim* h = b->reps[r];
+        Bundle* fit = nullptr;
+        for (Bundle& p : packs)
+            if ((int64_t)p.e.size() + h->S <= kBatchWarps) { fit = &p; break; }
+        if (!fit) { packs.push_back(Bundle{{}, 0.0}); fit = &packs.back(); }
+        for (int64_t t = 0; t < h->S; ++t) fit->e.push_back(make_int2(r, (int)t));
+        fit->work = std::max(fit->work, (double)h->R * h->half);
+    }
+    bundles.insert(bundles.end(), packs.begin(), packs.end());
+    std::stable_sort(bundles.begin(), bundles.end(), [](const Bundle& x, const Bundle& y) { return x.work > y.work; });
+    std::vector<int2> entries;
+    std::vector<int> boff(1, 0);
+    for (const Bundle& bd : bundles) {
+        entries.insert(entries.end(), bd.e.begin(), bd.e.end());
+        boff.push_back((int)entries.size());
+    }
+    b->nbundles = (int)bundles.size();
+
+    std::vector<FlipArgs> desc(2 * n);
+    for (int r = 0; r < 2 * n; ++r) desc[r] = make_flip_args(b->reps[r], 0);
+    isg_sim* h0 = b->reps[0];
+    b->d_reps = (FlipArgs*)dev_alloc(h0, desc.size() * sizeof(FlipArgs));
+    b->d_entries = (int2*)dev_alloc(h0, entries.size() * sizeof(int2));
+    b->d_boff = (int*)dev_alloc(h0, boff.size() * sizeof(int));
+    b->d_ctr = (unsigned*)dev_alloc(h0, 2 * sizeof(unsigned));
+    if (!b->d_reps || !b->d_entries || !b->d_boff || !b->d_ctr) {
+        batch_free(b);
+        set_error("isg_batch_create: device allocation failed");
+        return ISG_ERR_NOMEM;
+    }
+    cudaError_t e = cudaMemcpy(b->d_reps, desc.data(), desc.size() * sizeof(FlipArgs), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_entries, entries.data(), entries.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_boff, boff.data(), boff.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(b->d_ctr, 0, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) {
+        const size_t smem = batch_smem(rng_kind);
+        e = rng_kind == ISG_RNG_MT19937
+                ? cudaFuncSetAttribute(batch_kernel<ISG_RNG_MT19937>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem)
+                : cudaFuncSetAttribute(batch_kernel<ISG_RNG_MINSTD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        batch_free(b);
+        return cuda_fail(e, "isg_batch_create");
+    }
+    *out = b;
+    return ISG_OK;
+}
+
+void isg_batch_destroy(isg_batch* b) {
+    if (!b) return;
+    cudaDeviceSynchronize();
+    batch_free(b);
+}
+
+int isg_batch_info(const isg_batch* b, int* samples, int* bundles, int64_t* attempts_per_sweep) {
+    if (!b) { set_error("isg_batch_info: NULL batch"); return ISG_ERR_ARG; }
+    if (samples) *samples = b->n;
+    if (bundles) *bundles = b->nbundles;
+    if (attempts_per_sweep) *attempts_per_sweep = b->attempts_per_sweep;
+    return ISG_OK;
+}
+
+int isg_batch_member(isg_batch* b, int i, isg_sim** out) {
+    if (!b || !out || i < 0 || i >= 2 * b->n) { set_error("isg_batch_member: bad argument"); return ISG_ERR_ARG; }
+    *out = b->reps[i];
+    return ISG_OK;
+}
+
+int isg_batch_run(isg_batch* b, int64_t sweeps, int group_sweeps, void* cuda_stream) {
+    if (!b || sweeps < 0) { set_error("isg_batch_run: bad argument"); return ISG_ERR_ARG; }
+    if (group_sweeps <= 0) group_sweeps = 64;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const int64_t full = sweeps / group_sweeps;
+    const int rem = (int)(sweeps % group_sweeps);
+    cudaError_t e = cudaSuccess;
+    if (full > 0 && (!b->exec || b->graph_group != group_sweeps)) {
+        if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+        if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+        e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const cudaError_t le = batch_launch(b, group_sweeps, b->cap);
+            e = cudaStreamEndCapture(b->cap, &b->graph);
+            if (e == cudaSuccess) e = le;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "isg_batch_run: graph capture");
+        b->graph_group = group_sweeps;
+    }
+    for (int64_t g = 0; g < full && e == cudaSuccess; ++g) e = cudaGraphLaunch(b->exec, s);
+    if (e == cudaSuccess && rem > 0) e = batch_launch(b, rem, s);
+    if (e != cudaSuccess) return cuda_fail(e, "isg_batch_run");
+    for (isg_sim* h : b->reps) {
+        h->sweeps += sweeps;
+        h->last_stream = s;
+    }
+    return ISG_OK;
+}
+
+int isg_batch_measure(isg_batch* b, int64_t* E, int64_t* Q, void* cuda_stream) {
+    if (!b) { set_error("isg_batch_measure: NULL batch"); return ISG_ERR_ARG; }
+    for (int r = 0; E && r < 2 * b->n; ++r) {
+        const int rc = isg_energy(b->reps[r], &E[r], cuda_stream);
+        if (rc) return rc;
+    }
+    for (int s = 0; Q && s < b->n; ++s) {
+        const int rc = isg_overlap(b->reps[2 * s], b->reps[2 * s + 1], &Q[s], cuda_stream);
+        if (rc) return rc;
+    }
+    return ISG_OK;
+}
+
+int isg_batch_tracked(isg_batch* b, int64_t* E, uint64_t* H, void* cuda_stream) {
+    if (!b) { set_error("isg_batch_tracked: NULL batch"); return ISG_ERR_ARG; }
+    for (int r = 0; r < 2 * b->n; ++r) {
+        if (E) {
+            const int rc = isg_tracked_energy(b->reps[r], &E[r]);
+            if (rc) return rc;
+        }
+        if (H) {
+            const int rc = isg_hash(b->reps[r], &H[r], cuda_stream);
+            if (rc) return rc;
+        }
+    }
+    return ISG_OK;
+}
+
+}  // extern "C"

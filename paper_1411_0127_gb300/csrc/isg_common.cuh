@@ -94,6 +94,7 @@ struct FlipArgs {
     int L, half, W, nt, c;
     int64_t R, S, rows;
     uint32_t thr1, thr2, thr3;
+    uint32_t cmp1, cmp2, cmp3;   // compared with the generator value: MT19937 thr_k, MINSTD ceil(thr_k / 2)
     uint32_t* rng;
     uint32_t* rng_pos;
     long long* dE;
@@ -188,6 +189,7 @@ __device__ __forceinline__ Word row_down(Word cur, Word nb, int k, int nt) {
 // The opaque handle.
 struct isg_sim {
     int L = 0, half = 0, wbits = 0, W = 0, nt = 0;
+    bool force32 = false;               // 32-bit words whatever L (batch members)
     int kind = 0;
     double beta = 0.0;
     uint32_t thr[4] = {0, 0, 0, 0};
@@ -215,6 +217,9 @@ void set_error(const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
 void* dev_alloc(isg_sim* h, size_t n);
 void dev_free(isg_sim* h, void* p);
+int create_sim(int L, uint64_t seed_J, uint64_t seed_spin, double beta, int rng_kind, bool force32,
+               isg_sim** out);
+void destroy_sim(isg_sim* h);
 
 // kernels (launchers) implemented in the .cu files
 cudaError_t launch_init_planes(isg_sim* h, cudaStream_t s);

@@ -168,6 +168,15 @@ FlipArgs make_flip_args(isg_sim* h, int colour) {
     a.thr1 = h->thr[1];
     a.thr2 = h->thr[2];
     a.thr3 = h->thr[3];
+    if (h->kind == ISG_RNG_MT19937) {
+        a.cmp1 = h->thr[1];
+        a.cmp2 = h->thr[2];
+        a.cmp3 = h->thr[3];
+    } else {
+        a.cmp1 = (uint32_t)(((uint64_t)h->thr[1] + 1) / 2);
+        a.cmp2 = (uint32_t)(((uint64_t)h->thr[2] + 1) / 2);
+        a.cmp3 = (uint32_t)(((uint64_t)h->thr[3] + 1) / 2);
+    }
     a.rng = h->rng;
     a.rng_pos = h->rng_pos;
     a.dE = h->scal;

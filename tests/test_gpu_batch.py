@@ -1,0 +1,112 @@
+"""Batched persistent engine against lone lattices and the CPU oracle.  Every
+replica of a batch must follow, bit for bit, the trajectory of a lone handle
+with the same seeds (and so the oracle's): tolerance zero."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import OracleSim
+
+pytestmark = pytest.mark.gpu
+
+SIZES = (16, 32, 48, 64, 96, 128, 192)
+
+
+@pytest.fixture(scope="module")
+def isg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1411_0127_gb300 import build
+    build.build()
+    import paper_1411_0127_gb300 as m
+    return m
+
+
+def mixed(n_per_size=1, temps=(0.7, 1.1)):
+    L, J, S, B = [], [], [], []
+    s = 0
+    for size in SIZES:
+        for T in temps:
+            for _ in range(n_per_size):
+                L.append(size)
+                J.append(500 + s)
+                S += [2 * s + 11, 2 * s + 12]
+                B.append(1.0 / T)
+                s += 1
+    return L, J, S, B
+
+
+@pytest.mark.parametrize("kind", ["mt19937", "minstd"])
+def test_batch_matches_oracle(isg, kind):
+    L, J, S, B = mixed()
+    b = isg.Batch(L, J, S, B, kind)
+    b.run(8, group_sweeps=3)              # two graph replays of 3 sweeps, then 2 more
+    E, Q = b.measure()
+    Et, H = b.tracked()
+    assert np.array_equal(E, Et)
+    k = isg.RNG_KINDS[kind]
+    for s in range(len(L)):
+        o = [OracleSim(L[s], J[s], S[2 * s + j], B[s], k) for j in range(2)]
+        for j in range(2):
+            o[j].sweep(8, threads=8)
+            assert E[2 * s + j] == o[j].tracked_energy(), (s, j, L[s])
+            assert int(H[2 * s + j]) == o[j].hash(), (s, j)
+        assert Q[s] == o[0].overlap(o[1]), s
+        if L[s] <= 64:
+            assert np.array_equal(b.member(2 * s).read_spins(), o[0].spins())
+
+
+def test_batch_member_equals_lone_handle(isg):
+    L, J, S, B = mixed(n_per_size=2, temps=(0.9,))
+    b = isg.Batch(L, J, S, B, "mt19937")
+    lone = [isg.Sim(L[r // 2], J[r // 2], S[r], B[r // 2], "mt19937") for r in range(2 * len(L))]
+    for g in (5, 64):                     # group shorter and longer than the run
+        b.run(5, group_sweeps=g)
+        for m in lone:
+            m.sweep(5)
+        E, H = b.tracked()
+        for r, m in enumerate(lone):
+            assert H[r] == m.hash() and E[r] == m.tracked_energy(), (g, r, L[r // 2])
+    assert b.info()["samples"] == len(L)
+
+
+def test_full_batch_workload_sampled(isg):
+    """The 512-sample workload in the benchmark's launch configuration (one
+    graph-replayed persistent launch of 64 sweeps); energies and overlaps of one
+    sample per lattice size checked against the oracle, the energy bookkeeping
+    of every replica checked against its energy from scratch."""
+    from paper_1411_0127_gb300 import workloads
+    samples = workloads.batch_samples()
+    L = [x.L for x in samples]
+    b = isg.Batch(L, [x.seed_J for x in samples], [v for x in samples for v in x.seed_spin],
+                  [1.0 / x.T for x in samples], "mt19937")
+    info = b.info()
+    assert info["attempts_per_sweep"] == 2 * sum(v ** 3 for v in L)
+    b.run(64, group_sweeps=64)
+    E, Q = b.measure()
+    Et, H = b.tracked()
+    assert np.array_equal(E, Et)
+    N = np.array([v ** 3 for v in L])
+    assert (np.abs(Q) <= N).all()
+    picked = {}
+    for s, v in enumerate(L):
+        picked.setdefault(v, s)
+    for v, s in sorted(picked.items()):
+        x = samples[s]
+        for j in range(2):
+            o = OracleSim(x.L, x.seed_J, x.seed_spin[j], 1.0 / x.T, oracle.RNG_MT19937)
+            o.sweep(64, threads=16)
+            assert E[2 * s + j] == o.tracked_energy(), (v, s, j)
+            assert int(H[2 * s + j]) == o.hash(), (v, s, j)
+            if j == 0:
+                o0 = o
+            else:
+                assert Q[s] == o0.overlap(o), (v, s)
+
+
+def test_batch_rejects_bad_arguments(isg):
+    with pytest.raises(isg.IsgError):
+        isg.Batch([16, 15], [1, 2], [1, 2, 3, 4], [1.0, 1.0])
+    with pytest.raises(isg.IsgError):
+        isg.Batch([16], [1], [1, 2], [0.0])
