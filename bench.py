@@ -51,6 +51,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--plain-steps", type=int, default=300)
+    p.add_argument("--batch-groups", type=int, default=2, help="timed 64-sweep groups of the batched workload (0: skip)")
     return p.parse_args()
 
 
@@ -158,7 +159,7 @@ def traffic_from_profile(kind: str):
         return None
     h = hashlib.sha256()
     for name in sorted(os.listdir(src)):
-        if name.startswith("isg_flip") or name == "isg_common.cuh":
+        if name in ("isg_flip_fast.cu", "isg_stream.cuh", "isg_common.cuh"):
             h.update(open(os.path.join(src, name), "rb").read())
     digest = h.hexdigest()[:16]
     fields = {}
@@ -196,6 +197,48 @@ def cpu_baseline(w, target_s: float = 12.0) -> dict:
     return {"value": dt * 1e12 / attempts, "unit": UNIT, "cores": min(threads, m), "kind": "oracle",
             "sample": "red+blue passes over blocks of %d of the %d streams of the L=%d lattice (%d attempts, "
                       "%.1f s wall)" % (m, S, w.L, attempts, dt)}
+
+
+def batched_section(a, stream) -> dict:
+    """The 512-sample batched workload (two replicas each, L in {16..192}, T in
+    {0.7, 0.9, 1.1}, MT19937): psFlip of the persistent graph-replayed engine,
+    against sweeping every replica on its own, one lattice per launch, with the
+    plain per-colour kernel and with the fast kernel."""
+    import torch
+    import paper_1411_0127_gb300 as isg
+    from paper_1411_0127_gb300 import workloads
+    samples = workloads.batch_samples()
+    b = isg.Batch([x.L for x in samples], [x.seed_J for x in samples],
+                  [v for x in samples for v in x.seed_spin], [1.0 / x.T for x in samples], "mt19937")
+    attempts = b.info()["attempts_per_sweep"]
+    group = 64
+    b.run(group, group, stream)                      # warm-up (captures the graph)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.run(a.batch_groups * group, group, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    sweeps = a.batch_groups * group
+    out = {"workload": "512 samples x 2 replicas, L uniform over {16,32,48,64,96,128,192}, T over {0.7,0.9,1.1}, "
+                       "MT19937, sampler seed 7; %d attempts per sweep" % attempts,
+           "group_sweeps": group, "timed_sweeps": sweeps, "launches": a.batch_groups,
+           "psflip": ms * 1e9 / (sweeps * attempts),
+           "samples_sweeps_per_s": len(samples) * sweeps / (ms / 1e3)}
+    members = [b.member(r) for r in range(2 * len(samples))]
+    for name, fn in (("plain_one_sample_per_launch_psflip", "sweep_plain"),
+                     ("fast_one_sample_per_launch_psflip", "sweep")):
+        n = 2
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for m in members:
+            getattr(m, fn)(n, stream)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = p0.elapsed_time(p1) * 1e9 / (n * attempts)
+    b.close()
+    return out
 
 
 def run_ours(a, dist: Dist):
@@ -265,6 +308,8 @@ def run_ours(a, dist: Dist):
     e2e_s = dist.max(time.perf_counter() - t0, device="cuda")
     e2e_value = e2e_s * 1e12 / (n_e2e * N * dist.world)
 
+    batched = batched_section(a, stream) if a.batch_groups > 0 else None
+
     ops = OPS_PER_ATTEMPT[w.kind]
     achieved_tops = ops * attempts_per_launch / launch_s / 1e12
     hbm_gbs = BYTES_PER_ATTEMPT * attempts_per_launch / launch_s / 1e9
@@ -283,7 +328,8 @@ def run_ours(a, dist: Dist):
         "vs_baseline": None, "dtype": "u64", "data": "synthetic", "impl": "ours",
         "config": {**workload_config(w), "parallelism": "replicas only (one lattice per GPU)"},
         "plain_psflip": plain,
-        "batched_psflip": None,
+        "batched_psflip": batched["psflip"] if batched else None,
+        "batched": batched,
         "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
                      "frac": achieved_tops / ALU_PEAK_TOPS, "traffic": traffic,
                      "kernel": "flip (one colour pass)", "ops_per_attempt": ops,
