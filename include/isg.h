@@ -183,6 +183,44 @@ int isg_batch_measure(isg_batch *b, int64_t *E, int64_t *Q, void *cuda_stream);
  * pointer may be NULL. */
 int isg_batch_tracked(isg_batch *b, int64_t *E, uint64_t *H, void *cuda_stream);
 
+/* -------------------------------------------------------------- server --- */
+
+/* A request server for quench jobs (one lattice, isg_create arguments, and a
+ * number of sweeps) that serves them by continuous batching: jobs are admitted
+ * as they arrive, in arrival order, while their device memory fits
+ * hbm_budget_bytes and fewer than max_active jobs (<= 0: 4096) are on the
+ * device; every quantum of quantum_sweeps sweeps (<= 0: 64) sweeps all active
+ * jobs at once (small lattices in persistent bundle launches, lattices with
+ * more than 256 RNG streams each on a CUDA stream of its own, overlapping);
+ * finished jobs release their memory at once.  The paper has no serving layer;
+ * each job follows exactly the trajectory of a lone isg_create handle. */
+typedef struct isg_server isg_server;
+int isg_server_create(size_t hbm_budget_bytes, int quantum_sweeps, int max_active, isg_server **out);
+void isg_server_destroy(isg_server *s);
+
+/* Queue a job arriving arrival_s seconds after isg_server_run starts; *job_id
+ * numbers jobs 0, 1, ... in submission order.  Thread-safe.  ISG_ERR_ARG for
+ * invalid lattice arguments, sweeps < 0, or a job larger than the budget. */
+int isg_server_submit(isg_server *s, int L, uint64_t seed_J, uint64_t seed_spin, double beta, int rng_kind,
+                      int64_t sweeps, double arrival_s, int64_t *job_id);
+
+/* Serve every queued job, in real time, until all have finished (sync).
+ * time_limit_s > 0 stops with ISG_ERR_TIMEOUT once that many seconds have
+ * passed with jobs unfinished. */
+int isg_server_run(isg_server *s, double time_limit_s);
+
+/* Outcome of one job: status 2 = finished (1 active, 0 waiting, < 0 the
+ * ISG_ERR_* that failed it), energy from scratch, Zobrist hash, and arrival,
+ * admission and completion times in seconds from the start of the run.
+ * Latency = done - arrival.  Any output pointer may be NULL. */
+int isg_server_job(const isg_server *s, int64_t id, int *status, int64_t *E, uint64_t *H, double *arrival_s,
+                   double *admit_s, double *done_s);
+
+/* Statistics of the last run: quanta, spin-flip attempts, wall time, time with
+ * work on the device, peak active jobs and peak device bytes admitted. */
+int isg_server_stats(const isg_server *s, int64_t *iterations, int64_t *attempts, double *wall_s, double *busy_s,
+                     int *peak_active, size_t *peak_bytes);
+
 /* ------------------------------------------------------- no allocation --- */
 
 /* The energy of Eq. 1, like isg_energy, for callers that must not allocate

@@ -57,6 +57,12 @@ SIGNATURES = {
     "isg_batch_run": (_i32, [_vp, _i64, _i32, _vp]),
     "isg_batch_measure": (_i32, [_vp, _vp, _vp, _vp]),
     "isg_batch_tracked": (_i32, [_vp, _vp, _vp, _vp]),
+    "isg_server_create": (_i32, [_sz, _i32, _i32, _PP]),
+    "isg_server_destroy": (None, [_vp]),
+    "isg_server_submit": (_i32, [_vp, _i32, _u64, _u64, _dbl, _i32, _i64, _dbl, _vp]),
+    "isg_server_run": (_i32, [_vp, _dbl]),
+    "isg_server_job": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "isg_server_stats": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
 }
 
 
@@ -328,3 +334,51 @@ class Batch:
         H = np.empty(2 * self.n, dtype=np.uint64)
         _check(lib().isg_batch_tracked(self._h, _ptr(E), _ptr(H), _stream(stream)))
         return E, H
+
+
+class Server:
+    """Continuous-batching request server for quench jobs (see isg_server_*)."""
+
+    def __init__(self, hbm_budget_bytes: int = 150 * 10**9, quantum_sweeps: int = 64, max_active: int = 4096):
+        h = ctypes.c_void_p()
+        _check(lib().isg_server_create(int(hbm_budget_bytes), int(quantum_sweeps), int(max_active),
+                                       ctypes.byref(h)))
+        self._h = h.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().isg_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, L, seed_J, seed_spin, beta, rng_kind, sweeps, arrival_s=0.0) -> int:
+        kind = RNG_KINDS[rng_kind] if isinstance(rng_kind, str) else int(rng_kind)
+        jid = ctypes.c_int64()
+        _check(lib().isg_server_submit(self._h, int(L), int(seed_J) & (2**64 - 1), int(seed_spin) & (2**64 - 1),
+                                       float(beta), kind, int(sweeps), float(arrival_s), ctypes.byref(jid)))
+        return jid.value
+
+    def run(self, time_limit_s: float = 0.0):
+        _check(lib().isg_server_run(self._h, float(time_limit_s)))
+
+    def job(self, jid: int) -> dict:
+        st, E, H = ctypes.c_int(), ctypes.c_int64(), ctypes.c_uint64()
+        a, ad, d = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(lib().isg_server_job(self._h, int(jid), ctypes.byref(st), ctypes.byref(E), ctypes.byref(H),
+                                    ctypes.byref(a), ctypes.byref(ad), ctypes.byref(d)))
+        return {"status": st.value, "E": E.value, "H": H.value, "arrival": a.value, "admit": ad.value,
+                "done": d.value, "latency": d.value - a.value}
+
+    def stats(self) -> dict:
+        it, at = ctypes.c_int64(), ctypes.c_int64()
+        wall, busy = ctypes.c_double(), ctypes.c_double()
+        pa, pb = ctypes.c_int(), ctypes.c_size_t()
+        _check(lib().isg_server_stats(self._h, ctypes.byref(it), ctypes.byref(at), ctypes.byref(wall),
+                                      ctypes.byref(busy), ctypes.byref(pa), ctypes.byref(pb)))
+        return {"iterations": it.value, "attempts": at.value, "wall_s": wall.value, "busy_s": busy.value,
+                "peak_active": pa.value, "peak_bytes": pb.value}

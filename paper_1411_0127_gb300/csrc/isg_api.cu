@@ -164,6 +164,20 @@ int create_sim(int L, uint64_t seed_J, uint64_t seed_spin, double beta, int rng_
 
 void destroy_sim(isg_sim* h) { free_sim(h); }
 
+// Device bytes a handle of this size and kind holds (planes, streams, words).
+size_t sim_device_bytes(int L, int rng_kind, bool force32) {
+    const int half = L / 2;
+    const int w64 = (half + 63) / 64, w32 = (half + 31) / 32;
+    const int wbits = (2 * w64 == w32 && !force32) ? 64 : 32;
+    const int W = (half + wbits - 1) / wbits;
+    const int64_t rows = (int64_t)L * L;
+    int64_t R = 0, S = 0;
+    partition(L, &R, &S);
+    const int64_t plane = (rows * W * (wbits / 8) + 255) / 256 * 256;
+    const int64_t rng = rng_kind == ISG_RNG_MT19937 ? S * kMtN * 4 : S * 4;
+    return (size_t)(8 * plane + rng + S * 4 + 8 * (int64_t)sizeof(long long));
+}
+
 }  // namespace isg
 
 using namespace isg;

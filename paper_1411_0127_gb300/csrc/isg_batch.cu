@@ -24,6 +24,7 @@
 #include <new>
 #include <vector>
 
+#include "isg_bundles.cuh"
 #include "isg_stream.cuh"
 
 struct isg_batch {
@@ -50,6 +51,7 @@ struct BatchArgs {
     const FlipArgs* reps;
     const int2* entries;
     const int* boff;
+    const int* bsweeps;   // sweeps of each bundle in this launch, or NULL: `sweeps` for all
     int nbundles;
     int sweeps;
     unsigned* ctr;
@@ -70,13 +72,14 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) batch_kernel(BatchArgs b,
         __syncthreads();
         if (bid >= b.nbundles) break;
         const int e0 = b.boff[bid], n = b.boff[bid + 1] - e0;
+        const int sweeps = b.bsweeps ? b.bsweeps[bid] : b.sweeps;
         const bool resident = n <= kBatchWarps;
         StreamRegs st;
         if (resident && wid < n) {
             const int2 e = b.entries[e0 + wid];
             load_stream<KIND>(b.reps[e.x], e.y, ring, st, k, lane);
         }
-        for (int pass = 0; pass < 2 * b.sweeps; ++pass) {
+        for (int pass = 0; pass < 2 * sweeps; ++pass) {
             for (int j = wid; j < n; j += kBatchWarps) {
                 const int2 e = b.entries[e0 + j];
                 const FlipArgs& a = b.reps[e.x];
@@ -111,29 +114,93 @@ static size_t batch_smem(int kind) {
     return (size_t)kBatchWarps * (ring + 3 * kCondWords) * sizeof(uint32_t);
 }
 
-static int batch_grid(const isg_batch* b) {
+cudaError_t prepare_bundle_kernel(int kind) {
+    const int smem = (int)batch_smem(kind);
+    return kind == ISG_RNG_MT19937
+               ? cudaFuncSetAttribute(batch_kernel<ISG_RNG_MT19937>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
+               : cudaFuncSetAttribute(batch_kernel<ISG_RNG_MINSTD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+cudaError_t launch_bundle_kernel(int kind, const FlipArgs* reps, const int2* entries, const int* boff,
+                                 const int* bsweeps, int nbundles, int sweeps, unsigned* ctr, cudaStream_t s) {
+    if (nbundles <= 0) return cudaSuccess;
+    BatchArgs a;
+    a.reps = reps;
+    a.entries = entries;
+    a.boff = boff;
+    a.bsweeps = bsweeps;
+    a.nbundles = nbundles;
+    a.sweeps = sweeps;
+    a.ctr = ctr;
+    const StreamConst k = stream_const();
+    const size_t smem = batch_smem(kind);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return std::max(1, std::min(sms, b->nbundles));
-}
-
-static cudaError_t batch_launch(isg_batch* b, int sweeps, cudaStream_t s) {
-    BatchArgs a;
-    a.reps = b->d_reps;
-    a.entries = b->d_entries;
-    a.boff = b->d_boff;
-    a.nbundles = b->nbundles;
-    a.sweeps = sweeps;
-    a.ctr = b->d_ctr;
-    const StreamConst k = stream_const();
-    const size_t smem = batch_smem(b->kind);
-    const int grid = batch_grid(b);
-    if (b->kind == ISG_RNG_MT19937)
+    const int grid = std::max(1, std::min(sms, nbundles));
+    if (kind == ISG_RNG_MT19937)
         batch_kernel<ISG_RNG_MT19937><<<grid, kBatchWarps * 32, smem, s>>>(a, k);
     else
         batch_kernel<ISG_RNG_MINSTD><<<grid, kBatchWarps * 32, smem, s>>>(a, k);
     return cudaGetLastError();
+}
+
+void plan_bundles(const std::vector<isg_sim*>& reps, std::vector<int2>& entries, std::vector<int>& boff,
+                  std::vector<int>* order) {
+    struct Bundle {
+        std::vector<int2> e;
+        std::vector<int> members;
+        double work;
+    };
+    std::vector<Bundle> bundles;
+    std::vector<int> small;
+    const int nrep = (int)reps.size();
+    for (int r = 0; r < nrep; ++r) {
+        const isg_sim* h = reps[r];
+        if (h->S > kBatchWarps) {
+            Bundle bd;
+            for (int64_t t = 0; t < h->S; ++t) bd.e.push_back(make_int2(r, (int)t));
+            bd.members.push_back(r);
+            bd.work = (double)((h->S + kBatchWarps - 1) / kBatchWarps) * (double)h->R * h->half;
+            bundles.push_back(bd);
+        } else {
+            small.push_back(r);
+        }
+    }
+    std::stable_sort(small.begin(), small.end(), [&](int x, int y) {
+        const isg_sim *a = reps[x], *c = reps[y];
+        if (a->S != c->S) return a->S > c->S;
+        return a->L > c->L;
+    });
+    std::vector<Bundle> packs;
+    for (int r : small) {
+        const isg_sim* h = reps[r];
+        Bundle* fit = nullptr;
+        for (Bundle& p : packs)
+            if ((int64_t)p.e.size() + h->S <= kBatchWarps) { fit = &p; break; }
+        if (!fit) { packs.push_back(Bundle{{}, {}, 0.0}); fit = &packs.back(); }
+        for (int64_t t = 0; t < h->S; ++t) fit->e.push_back(make_int2(r, (int)t));
+        fit->members.push_back(r);
+        fit->work = std::max(fit->work, (double)h->R * h->half);
+    }
+    bundles.insert(bundles.end(), packs.begin(), packs.end());
+    std::stable_sort(bundles.begin(), bundles.end(), [](const Bundle& x, const Bundle& y) { return x.work > y.work; });
+    entries.clear();
+    boff.assign(1, 0);
+    if (order) order->clear();
+    for (const Bundle& bd : bundles) {
+        entries.insert(entries.end(), bd.e.begin(), bd.e.end());
+        boff.push_back((int)entries.size());
+        if (order) {  // members of each bundle, -1 terminated
+            order->insert(order->end(), bd.members.begin(), bd.members.end());
+            order->push_back(-1);
+        }
+    }
+}
+
+static cudaError_t batch_launch(isg_batch* b, int sweeps, cudaStream_t s) {
+    return launch_bundle_kernel(b->kind, b->d_reps, b->d_entries, b->d_boff, nullptr, b->nbundles, sweeps,
+                                b->d_ctr, s);
 }
 
 static void batch_free(isg_batch* b) {
@@ -184,47 +251,10 @@ int isg_batch_create(int n, const int* L, const uint64_t* seed_J, const uint64_t
     }
 
     // bundles: big lattices alone, small ones first-fit into 32 entries
-    struct Bundle {
-        std::vector<int2> e;
-        double work;
-    };
-    std::vector<Bundle> bundles;
-    std::vector<int> small;
-    for (int r = 0; r < 2 * n; ++r) {
-        const isg_sim* h = b->reps[r];
-        if (h->S > kBatchWarps) {
-            Bundle bd;
-            for (int64_t t = 0; t < h->S; ++t) bd.e.push_back(make_int2(r, (int)t));
-            bd.work = (double)((h->S + kBatchWarps - 1) / kBatchWarps) * (double)h->R * h->half;
-            bundles.push_back(bd);
-        } else {
-            small.push_back(r);
-        }
-    }
-    std::stable_sort(small.begin(), small.end(), [&](int x, int y) {
-        const isg_sim *a = b->reps[x], *c = b->reps[y];
-        if (a->S != c->S) return a->S > c->S;
-        return a->L > c->L;
-    });
-    std::vector<Bundle> packs;
-    for (int r : small) {
-        const isg_sim* h = b->reps[r];
-        Bundle* fit = nullptr;
-        for (Bundle& p : packs)
-            if ((int64_t)p.e.size() + h->S <= kBatchWarps) { fit = &p; break; }
-        if (!fit) { packs.push_back(Bundle{{}, 0.0}); fit = &packs.back(); }
-        for (int64_t t = 0; t < h->S; ++t) fit->e.push_back(make_int2(r, (int)t));
-        fit->work = std::max(fit->work, (double)h->R * h->half);
-    }
-    bundles.insert(bundles.end(), packs.begin(), packs.end());
-    std::stable_sort(bundles.begin(), bundles.end(), [](const Bundle& x, const Bundle& y) { return x.work > y.work; });
     std::vector<int2> entries;
-    std::vector<int> boff(1, 0);
-    for (const Bundle& bd : bundles) {
-        entries.insert(entries.end(), bd.e.begin(), bd.e.end());
-        boff.push_back((int)entries.size());
-    }
-    b->nbundles = (int)bundles.size();
+    std::vector<int> boff;
+    plan_bundles(b->reps, entries, boff, nullptr);
+    b->nbundles = (int)boff.size() - 1;
 
     std::vector<FlipArgs> desc(2 * n);
     for (int r = 0; r < 2 * n; ++r) desc[r] = make_flip_args(b->reps[r], 0);
@@ -243,14 +273,7 @@ int isg_batch_create(int n, const int* L, const uint64_t* seed_J, const uint64_t
         e = cudaMemcpy(b->d_entries, entries.data(), entries.size() * sizeof(int2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_boff, boff.data(), boff.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(b->d_ctr, 0, 2 * sizeof(unsigned));
-    if (e == cudaSuccess) {
-        const size_t smem = batch_smem(rng_kind);
-        e = rng_kind == ISG_RNG_MT19937
-                ? cudaFuncSetAttribute(batch_kernel<ISG_RNG_MT19937>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem)
-                : cudaFuncSetAttribute(batch_kernel<ISG_RNG_MINSTD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-    }
+    if (e == cudaSuccess) e = prepare_bundle_kernel(rng_kind);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         batch_free(b);

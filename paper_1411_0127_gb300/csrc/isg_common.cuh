@@ -220,6 +220,7 @@ void dev_free(isg_sim* h, void* p);
 int create_sim(int L, uint64_t seed_J, uint64_t seed_spin, double beta, int rng_kind, bool force32,
                isg_sim** out);
 void destroy_sim(isg_sim* h);
+size_t sim_device_bytes(int L, int rng_kind, bool force32);
 
 // kernels (launchers) implemented in the .cu files
 cudaError_t launch_init_planes(isg_sim* h, cudaStream_t s);
