@@ -52,6 +52,7 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--plain-steps", type=int, default=300)
     p.add_argument("--batch-groups", type=int, default=2, help="timed 64-sweep groups of the batched workload (0: skip)")
+    p.add_argument("--serve-jobs", type=int, default=16, help="jobs of the serving trace to serve (0: skip)")
     return p.parse_args()
 
 
@@ -241,6 +242,33 @@ def batched_section(a, stream) -> dict:
     return out
 
 
+def serving_section(a) -> dict:
+    """The first `--serve-jobs` jobs of the Poisson quench trace (200 jobs/s,
+    L over even multiples of 16 in [32, 512], sweeps log-uniform in [1e2, 1e5],
+    T uniform in [0.5, 1.5], MINSTD or MT19937) served by continuous batching
+    under a 150 GB budget; latency = completion - arrival, queueing included."""
+    import numpy as np
+    import paper_1411_0127_gb300 as isg
+    from paper_1411_0127_gb300 import workloads
+    jobs = workloads.serving_trace(a.serve_jobs)
+    srv = isg.Server(150 * 10**9, 64, 4096)
+    ids = [srv.submit(j.L, j.seed_J, j.seed_spin, 1.0 / j.T, j.kind, j.sweeps, j.arrival) for j in jobs]
+    srv.run(time_limit_s=600)
+    res = [srv.job(i) for i in ids]
+    st = srv.stats()
+    srv.close()
+    lat = np.array([r["latency"] for r in res])
+    queue = np.array([r["admit"] - r["arrival"] for r in res])
+    return {"trace": "first %d jobs of the Poisson trace (200 jobs/s, arrival seed 11), %.3g attempts, "
+                     "arrivals over %.3f s" % (len(jobs), st["attempts"], jobs[-1].arrival),
+            "jobs": len(jobs), "finished": sum(r["status"] == 2 for r in res),
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "mean_admission_wait_s": float(queue.mean()),
+            "aggregate_psflip": st["busy_s"] * 1e12 / max(1, st["attempts"]),
+            "wall_s": st["wall_s"], "quanta": st["iterations"], "peak_active": st["peak_active"],
+            "peak_bytes": st["peak_bytes"], "budget_bytes": 150 * 10**9, "quantum_sweeps": 64}
+
+
 def run_ours(a, dist: Dist):
     import numpy as np
     import torch
@@ -309,6 +337,7 @@ def run_ours(a, dist: Dist):
     e2e_value = e2e_s * 1e12 / (n_e2e * N * dist.world)
 
     batched = batched_section(a, stream) if a.batch_groups > 0 else None
+    serving = serving_section(a) if a.serve_jobs > 0 and dist.rank == 0 else None
 
     ops = OPS_PER_ATTEMPT[w.kind]
     achieved_tops = ops * attempts_per_launch / launch_s / 1e12
@@ -330,6 +359,7 @@ def run_ours(a, dist: Dist):
         "plain_psflip": plain,
         "batched_psflip": batched["psflip"] if batched else None,
         "batched": batched,
+        "serving": serving,
         "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
                      "frac": achieved_tops / ALU_PEAK_TOPS, "traffic": traffic,
                      "kernel": "flip (one colour pass)", "ops_per_attempt": ops,

@@ -102,6 +102,39 @@ __device__ __forceinline__ void mt_pair(uint32_t* ring, int& iA, uint32_t& dA, u
     dB = mt_temper_mul(vB, k);
 }
 
+// Four 32-draw blocks (128 draws) at once: block j reads x_{k+32j+l+397}, which
+// was written 227 - 32j - l >= 100 draws before this step, and no block reads a
+// word another block of the step writes after the barrier.
+__device__ __forceinline__ void mt_quad(uint32_t* ring, int& i0, uint32_t d[4], const MtMul& k) {
+    int i[4];
+    i[0] = i0;
+#pragma unroll
+    for (int j = 1; j < 4; ++j) {
+        const int v = i[j - 1] + 32;
+        i[j] = v >= kMtN ? v - kMtN : v;
+    }
+    uint32_t a[4], b[4], m[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        a[j] = ring[i[j]];
+        b[j] = ring[i[j] + 1];
+        m[j] = ring[i[j] + kMtM];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t v = mt_twist(a[j], b[j], m[j], k);
+        ring[i[j]] = v;
+        ring[i[j] + kMtN] = v;
+        d[j] = v;
+    }
+    __syncwarp();
+    const int v = i[3] + 32;
+    i0 = v >= kMtN ? v - kMtN : v;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) d[j] = mt_temper_mul(d[j], k);
+}
+
 // One block of up to 32 draws (tail of a row group); lanes >= nvalid consume nothing.
 __device__ __forceinline__ uint32_t mt_single(uint32_t* ring, int& iA, int lane, int nvalid, const MtMul& k) {
     const uint32_t a = ring[iA], b = ring[iA + 1], m = ring[iA + kMtM];
@@ -226,7 +259,25 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t t,
     for (int64_t g0 = r_begin; g0 < r_end; g0 += G) {
         const int nrows = (int)((r_end - g0) < G ? (r_end - g0) : G);
         const int D = nrows * half;
-        const int npairs = D >> 6;
+        const int nquads = kMT ? (D >> 7) : 0;
+        for (int q = 0; q < nquads; ++q) {
+            uint32_t d[4], c4[4], c8[4], c12[4];
+            mt_quad(ring, st.iA, d, k.mul);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                c4[j] = __ballot_sync(kFull, d[j] < a.cmp1);
+                c8[j] = __ballot_sync(kFull, d[j] < a.cmp2);
+                c12[j] = __ballot_sync(kFull, d[j] < a.cmp3);
+            }
+            if (lane == 0) {
+                *(uint4*)(cond + 4 * q) = make_uint4(c4[0], c4[1], c4[2], c4[3]);
+                *(uint4*)(cond + kCondWords + 4 * q) = make_uint4(c8[0], c8[1], c8[2], c8[3]);
+                *(uint4*)(cond + 2 * kCondWords + 4 * q) = make_uint4(c12[0], c12[1], c12[2], c12[3]);
+            }
+        }
+        uint32_t* cw = cond + 4 * nquads;  // the pair and single steps continue the bit streams here
+        const int Dq = D - (nquads << 7);
+        const int npairs = Dq >> 6;
         for (int q = 0; q < npairs; ++q) {
             uint32_t dA, dB;
             if (kMT) {
@@ -241,12 +292,12 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t t,
             const uint32_t A8 = __ballot_sync(kFull, dA < a.cmp2), B8 = __ballot_sync(kFull, dB < a.cmp2);
             const uint32_t A12 = __ballot_sync(kFull, dA < a.cmp3), B12 = __ballot_sync(kFull, dB < a.cmp3);
             if (lane == 0) {
-                *(uint2*)(cond + 2 * q) = make_uint2(A4, B4);
-                *(uint2*)(cond + kCondWords + 2 * q) = make_uint2(A8, B8);
-                *(uint2*)(cond + 2 * kCondWords + 2 * q) = make_uint2(A12, B12);
+                *(uint2*)(cw + 2 * q) = make_uint2(A4, B4);
+                *(uint2*)(cw + kCondWords + 2 * q) = make_uint2(A8, B8);
+                *(uint2*)(cw + 2 * kCondWords + 2 * q) = make_uint2(A12, B12);
             }
         }
-        int rem = D - (npairs << 6);
+        int rem = Dq - (npairs << 6);
         int b = 2 * npairs;
         while (rem > 0) {
             const int nvalid = rem < 32 ? rem : 32;
@@ -265,9 +316,9 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t t,
             const uint32_t m8 = __ballot_sync(kFull, d < a.cmp2);
             const uint32_t m12 = __ballot_sync(kFull, d < a.cmp3);
             if (lane == 0) {
-                cond[b] = m4;
-                cond[kCondWords + b] = m8;
-                cond[2 * kCondWords + b] = m12;
+                cw[b] = m4;
+                cw[kCondWords + b] = m8;
+                cw[2 * kCondWords + b] = m12;
             }
             ++b;
             rem -= nvalid;
