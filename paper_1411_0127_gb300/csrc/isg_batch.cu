@@ -46,6 +46,7 @@ struct isg_batch {
 namespace isg {
 
 constexpr int kBatchWarps = 32;
+constexpr int kBatchSlack = 512;  // MT19937 window per warp: 624 + 512 words (32 warps fit 227 KiB)
 
 struct BatchArgs {
     const FlipArgs* reps;
@@ -61,9 +62,9 @@ template <int KIND>
 __global__ void __launch_bounds__(kBatchWarps * 32, 1) batch_kernel(BatchArgs b, StreamConst k) {
     extern __shared__ uint32_t smem[];
     __shared__ int s_bundle;
-    constexpr int kRing = KIND == ISG_RNG_MT19937 ? 2 * kMtN : 0;
+    constexpr int kRing = KIND == ISG_RNG_MT19937 ? mt_window(kBatchSlack) : 0;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    uint32_t* ring = smem + wid * (kRing + 3 * kCondWords);
+    uint32_t* ring = smem + wid * (kRing + 2 * kCondWords);
     uint32_t* cond = ring + kRing;
     for (;;) {
         if (threadIdx.x == 0) s_bundle = (int)atomicAdd(&b.ctr[0], 1u);
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) batch_kernel(BatchArgs b,
                 const FlipArgs& a = b.reps[e.x];
                 if (!resident) load_stream<KIND>(a, e.y, ring, st, k, lane);
                 int dE = 0;
-                stream_pass<uint32_t, KIND>(a, pass & 1, e.y, ring, cond, st, k, lane, dE);
+                stream_pass<uint32_t, KIND, kBatchSlack>(a, pass & 1, e.y, ring, cond, st, k, lane, dE);
                 if (!resident) store_stream<KIND>(a, e.y, ring, st, lane);
                 for (int sh = 16; sh; sh >>= 1) dE += __shfl_xor_sync(kFull, dE, sh);
                 if (lane == 0 && dE != 0) atomicAdd((unsigned long long*)a.dE, (unsigned long long)(long long)dE);
@@ -110,8 +111,8 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) batch_kernel(BatchArgs b,
 }
 
 static size_t batch_smem(int kind) {
-    const int ring = kind == ISG_RNG_MT19937 ? 2 * kMtN : 0;
-    return (size_t)kBatchWarps * (ring + 3 * kCondWords) * sizeof(uint32_t);
+    const int ring = kind == ISG_RNG_MT19937 ? mt_window(kBatchSlack) : 0;
+    return (size_t)kBatchWarps * (ring + 2 * kCondWords) * sizeof(uint32_t);
 }
 
 cudaError_t prepare_bundle_kernel(int kind) {

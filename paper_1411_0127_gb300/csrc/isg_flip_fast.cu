@@ -11,6 +11,7 @@
 namespace isg {
 
 constexpr int kFastWarps = 4;
+constexpr int kFastSlack = 1024;  // MT19937 window: 624 live words + 1024 free (6.6 KiB per warp)
 
 struct Tickets {
     unsigned long long* counter;  // device word, only ever incremented
@@ -18,11 +19,12 @@ struct Tickets {
 };
 
 template <typename Word, int KIND>
-__global__ void __launch_bounds__(kFastWarps * 32, 8) flip_fast_kernel(FlipArgs a, StreamConst k, Tickets tk) {
+__global__ void __launch_bounds__(kFastWarps * 32, KIND == ISG_RNG_MT19937 ? 7 : 8)
+    flip_fast_kernel(FlipArgs a, StreamConst k, Tickets tk) {
     extern __shared__ uint32_t smem[];
-    constexpr int kRing = KIND == ISG_RNG_MT19937 ? 2 * kMtN : 0;
+    constexpr int kRing = KIND == ISG_RNG_MT19937 ? mt_window(kFastSlack) : 0;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    uint32_t* ring = smem + wid * (kRing + 3 * kCondWords);
+    uint32_t* ring = smem + wid * (kRing + 2 * kCondWords);
     uint32_t* cond = ring + kRing;
     int dEsum = 0;
     for (;;) {
@@ -33,7 +35,7 @@ __global__ void __launch_bounds__(kFastWarps * 32, 8) flip_fast_kernel(FlipArgs 
         if (t >= a.S) break;
         StreamRegs st;
         load_stream<KIND>(a, t, ring, st, k, lane);
-        stream_pass<Word, KIND>(a, a.c, t, ring, cond, st, k, lane, dEsum);
+        stream_pass<Word, KIND, kFastSlack>(a, a.c, t, ring, cond, st, k, lane, dEsum);
         store_stream<KIND>(a, t, ring, st, lane);
     }
     for (int sh = 16; sh; sh >>= 1) dEsum += __shfl_xor_sync(kFull, dEsum, sh);
@@ -47,8 +49,8 @@ static cudaError_t launch_fast_t(isg_sim* h, int colour, cudaStream_t s) {
     Tickets tk;
     tk.counter = (unsigned long long*)(h->scal + 3);
     tk.base = h->tickets;
-    constexpr int kRing = KIND == ISG_RNG_MT19937 ? 2 * kMtN : 0;
-    const size_t smem = (size_t)kFastWarps * (kRing + 3 * kCondWords) * sizeof(uint32_t);
+    constexpr int kRing = KIND == ISG_RNG_MT19937 ? mt_window(kFastSlack) : 0;
+    const size_t smem = (size_t)kFastWarps * (kRing + 2 * kCondWords) * sizeof(uint32_t);
     static int sms = 0;
     static int per_sm[2][2] = {{0, 0}, {0, 0}};
     int& occ = per_sm[sizeof(Word) == 8][KIND];

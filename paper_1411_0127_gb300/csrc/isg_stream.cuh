@@ -4,19 +4,26 @@
 // A stream owns R consecutive rows r = y + L*z of a lattice.  The warp walks
 // them in groups of G = 32 / W rows (W words per row and colour), one word of
 // the group per lane:
-//   1. draw phase: the group's draws are produced 64 at a time in stream order
-//      (row by row, ascending x), compared with the three integer thresholds
-//      (Sec. 4: R < Rmax exp(-beta dE)) and the three ballots stored as bit
-//      streams in shared memory;
+//   1. draw phase: the group's draws are produced 128 at a time in stream order
+//      (row by row, ascending x) and compared with the three integer thresholds
+//      thr1 > thr2 > thr3 (Sec. 4: R < Rmax exp(-beta dE)).  Because the three
+//      comparisons are nested, a draw's outcome is a level 0..3 (how many
+//      thresholds it is below), and two ballots per 32 draws carry it: "lo" =
+//      level odd, "hi" = level >= 2; they are stored as bit streams in shared
+//      memory;
 //   2. logic phase: each lane loads its word of S_c, its forward couplings and
 //      the other colour's neighbour words, counts unsatisfied bonds with a
-//      bit-sliced adder, cuts its window out of the ballot bit streams, forms
-//      the flip mask, XORs it into S_c and sums dE = 12 - 4u.
+//      bit-sliced adder, cuts its window out of the two bit streams
+//      (d < thr1 = lo | hi, d < thr2 = hi, d < thr3 = lo & hi), forms the flip
+//      mask, XORs it into S_c and sums dE = 12 - 4u.
 //
 // Generators (Sec. 3):
-//   * MT19937 keeps its 624 words twice in shared memory (slot s and s + 624
-//     hold the same word), so x_{k+1} and x_{k+397} sit at fixed offsets from
-//     one index; its shifts run as multiplies (MtMul) on the FMA pipe;
+//   * MT19937 keeps its words in a linear window of shared memory: B[j] holds
+//     x_{base + j}, x_{k+624} is appended at B[k - base + 624], and when the
+//     free slots run out the 624 live words move back to the front; the reads
+//     x_k, x_{k+1}, x_{k+397} are fixed offsets from one index with no
+//     wrap-around arithmetic.  Its shifts run as multiplies (MtMul) on the FMA
+//     pipe;
 //   * MINSTD keeps two lanes' worth of states (positions +1..+32 and +33..+64)
 //     and compares the state x with ceil(thr / 2) (d = 2x < thr <=> x <
 //     ceil(thr / 2)).
@@ -59,6 +66,9 @@ inline StreamConst stream_const() {
     return k;
 }
 
+// Shared-memory words of one warp's MT19937 window with `slack` free slots.
+constexpr int mt_window(int slack) { return kMtN + slack; }
+
 // MT19937 twist of one word: x_{k+624} from x_k, x_{k+1}, x_{k+397}.  The odd
 // test uses b - 2 (b >> 1) = b & 1.
 __device__ __forceinline__ uint32_t mt_twist(uint32_t a, uint32_t b, uint32_t m, const MtMul& k) {
@@ -78,75 +88,66 @@ __device__ __forceinline__ uint32_t mt_temper_mul(uint32_t v, const MtMul& k) {
     return v;
 }
 
-// Two 32-draw blocks of an MT19937 stream held in a mirrored 1248-word ring.
-// iA = (k + lane) mod 624 for the first block's draw k + lane; on return it
-// points 64 draws further.  Reads of both blocks precede all writes (one warp
-// barrier between): block B's inputs x_{k+32+l+397} were written 195 or more
-// draws earlier, and the words both blocks overwrite are read first.
-__device__ __forceinline__ void mt_pair(uint32_t* ring, int& iA, uint32_t& dA, uint32_t& dB, const MtMul& k) {
-    int iB = iA + 32;
-    iB = iB >= kMtN ? iB - kMtN : iB;
-    const uint32_t aA = ring[iA], bA = ring[iA + 1], mA = ring[iA + kMtM];
-    const uint32_t aB = ring[iB], bB = ring[iB + 1], mB = ring[iB + kMtM];
+// Make room for `need` more words: if the window is full, move the 624 live
+// words B[iA .. iA+623] to the front (all read before any is written).
+template <int SLACK>
+__device__ __forceinline__ void mt_make_room(uint32_t* B, int& iA, int need, int lane) {
+    if (iA + kMtN + need <= mt_window(SLACK)) return;
     __syncwarp();
-    const uint32_t vA = mt_twist(aA, bA, mA, k);
-    const uint32_t vB = mt_twist(aB, bB, mB, k);
-    ring[iA] = vA;
-    ring[iA + kMtN] = vA;
-    ring[iB] = vB;
-    ring[iB + kMtN] = vB;
+    uint32_t v[20];
+#pragma unroll
+    for (int q = 0; q < 20; ++q) v[q] = (lane + 32 * q < kMtN) ? B[iA + lane + 32 * q] : 0u;
     __syncwarp();
-    iA = iB + 32;
-    iA = iA >= kMtN ? iA - kMtN : iA;
-    dA = mt_temper_mul(vA, k);
-    dB = mt_temper_mul(vB, k);
+#pragma unroll
+    for (int q = 0; q < 20; ++q)
+        if (lane + 32 * q < kMtN) B[lane + 32 * q] = v[q];
+    __syncwarp();
+    iA = 0;
 }
 
-// Four 32-draw blocks (128 draws) at once: block j reads x_{k+32j+l+397}, which
-// was written 227 - 32j - l >= 100 draws before this step, and no block reads a
-// word another block of the step writes after the barrier.
-__device__ __forceinline__ void mt_quad(uint32_t* ring, int& i0, uint32_t d[4], const MtMul& k) {
-    int i[4];
-    i[0] = i0;
-#pragma unroll
-    for (int j = 1; j < 4; ++j) {
-        const int v = i[j - 1] + 32;
-        i[j] = v >= kMtN ? v - kMtN : v;
-    }
+// Four 32-draw blocks (128 draws) at once.  Block j reads x_{k+32j+l+397},
+// which was appended 227 - 32j - l >= 100 draws before this step, so every
+// read of the step can precede every write (one warp barrier between).
+template <int SLACK>
+__device__ __forceinline__ void mt_quad(uint32_t* B, int& iA, int& pos, uint32_t d[4], const MtMul& k, int lane) {
+    mt_make_room<SLACK>(B, iA, 128, lane);
     uint32_t a[4], b[4], m[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        a[j] = ring[i[j]];
-        b[j] = ring[i[j] + 1];
-        m[j] = ring[i[j] + kMtM];
+        const int i = iA + 32 * j + lane;
+        a[j] = B[i];
+        b[j] = B[i + 1];
+        m[j] = B[i + kMtM];
     }
     __syncwarp();
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const uint32_t v = mt_twist(a[j], b[j], m[j], k);
-        ring[i[j]] = v;
-        ring[i[j] + kMtN] = v;
+        B[iA + 32 * j + lane + kMtN] = v;
         d[j] = v;
     }
     __syncwarp();
-    const int v = i[3] + 32;
-    i0 = v >= kMtN ? v - kMtN : v;
+    iA += 128;
+    pos += 128;
+    pos = pos >= kMtN ? pos - kMtN : pos;
 #pragma unroll
     for (int j = 0; j < 4; ++j) d[j] = mt_temper_mul(d[j], k);
 }
 
 // One block of up to 32 draws (tail of a row group); lanes >= nvalid consume nothing.
-__device__ __forceinline__ uint32_t mt_single(uint32_t* ring, int& iA, int lane, int nvalid, const MtMul& k) {
-    const uint32_t a = ring[iA], b = ring[iA + 1], m = ring[iA + kMtM];
+template <int SLACK>
+__device__ __forceinline__ uint32_t mt_single(uint32_t* B, int& iA, int& pos, int lane, int nvalid,
+                                              const MtMul& k) {
+    mt_make_room<SLACK>(B, iA, 32, lane);
+    const int i = iA + lane;
+    const uint32_t a = B[i], b = B[i + 1], m = B[i + kMtM];
     __syncwarp();
     const uint32_t v = mt_twist(a, b, m, k);
-    if (lane < nvalid) {
-        ring[iA] = v;
-        ring[iA + kMtN] = v;
-    }
+    if (lane < nvalid) B[i + kMtN] = v;
     __syncwarp();
     iA += nvalid;
-    iA = iA >= kMtN ? iA - kMtN : iA;
+    pos += nvalid;
+    pos = pos >= kMtN ? pos - kMtN : pos;
     return mt_temper_mul(v, k);
 }
 
@@ -193,10 +194,9 @@ __device__ __forceinline__ void word_update(const FlipArgs& a, int c, int r, int
     }
     Word u0, u1, u2;
     Logic<Word>::count6(e_xp, e_xm, e_yp, e_ym, e_zp, e_zm, u0, u1, u2);
-    const Word c4 = take_bits<Word>(cond, off);
-    const Word c8 = take_bits<Word>(cond + kCondWords, off);
-    const Word c12 = take_bits<Word>(cond + 2 * kCondWords, off);
-    Word f = Logic<Word>::flip(u0, u1, u2, c4, c8, c12);
+    const Word lo = take_bits<Word>(cond, off);
+    const Word hi = take_bits<Word>(cond + kCondWords, off);
+    Word f = Logic<Word>::flip(u0, u1, u2, lo | hi, hi, lo & hi);
     if (k == W - 1 && nt < w) f &= (Word)((Word(1) << nt) - 1);
     Sc[o] = s ^ f;
     dEsum += Logic<Word>::dE(f, u0, u1, u2);
@@ -204,22 +204,26 @@ __device__ __forceinline__ void word_update(const FlipArgs& a, int c, int r, int
 
 // Generator state of the stream a warp is working on.
 struct StreamRegs {
-    int iA;        // MT19937: (next draw + lane) mod 624 in the ring
+    int pos;       // MT19937: position (mod 624) of the next draw in the stored ring
+    int iA;        // MT19937: window index of x_k for the next draw k
     uint32_t xA;   // MINSTD: state of draw n + lane + 1
     uint32_t xB;   // MINSTD: state of draw n + lane + 33
 };
 
+// The stored MT19937 state is a 624-word ring with the position of the next
+// draw; it is unrolled into the front of the window on load and rolled back on
+// store, so the stored format does not depend on the window.
 template <int KIND>
-__device__ __forceinline__ void load_stream(const FlipArgs& a, int64_t t, uint32_t* ring, StreamRegs& st,
+__device__ __forceinline__ void load_stream(const FlipArgs& a, int64_t t, uint32_t* B, StreamRegs& st,
                                             const StreamConst& k, int lane) {
     if (KIND == ISG_RNG_MT19937) {
-        for (int i = lane; i < kMtN; i += 32) {
-            const uint32_t v = a.rng[t * kMtN + i];
-            ring[i] = v;
-            ring[i + kMtN] = v;
+        const int p = (int)a.rng_pos[t];
+        for (int j = lane; j < kMtN; j += 32) {
+            const int s = p + j >= kMtN ? p + j - kMtN : p + j;
+            B[j] = a.rng[t * kMtN + s];
         }
-        const int i = (int)a.rng_pos[t] + lane;
-        st.iA = i >= kMtN ? i - kMtN : i;
+        st.pos = p;
+        st.iA = 0;
         __syncwarp();
     } else {
         st.xA = minstd_mulmod(a.rng[t], a.mt.pow[lane + 1]);
@@ -228,13 +232,15 @@ __device__ __forceinline__ void load_stream(const FlipArgs& a, int64_t t, uint32
 }
 
 template <int KIND>
-__device__ __forceinline__ void store_stream(const FlipArgs& a, int64_t t, const uint32_t* ring,
+__device__ __forceinline__ void store_stream(const FlipArgs& a, int64_t t, const uint32_t* B,
                                              const StreamRegs& st, int lane) {
     if (KIND == ISG_RNG_MT19937) {
         __syncwarp();
-        for (int i = lane; i < kMtN; i += 32) a.rng[t * kMtN + i] = ring[i];
-        const int pos = __shfl_sync(kFull, st.iA, 0);
-        if (lane == 0) a.rng_pos[t] = (uint32_t)pos;
+        for (int j = lane; j < kMtN; j += 32) {
+            const int s = st.pos + j >= kMtN ? st.pos + j - kMtN : st.pos + j;
+            a.rng[t * kMtN + s] = B[st.iA + j];
+        }
+        if (lane == 0) a.rng_pos[t] = (uint32_t)st.pos;
         __syncwarp();
     } else {
         const uint32_t x0 = __shfl_sync(kFull, st.xA, 0);
@@ -242,9 +248,15 @@ __device__ __forceinline__ void store_stream(const FlipArgs& a, int64_t t, const
     }
 }
 
-// One pass of colour c over stream t; the stream state is in ring / st.
-template <typename Word, int KIND>
-__device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t t, uint32_t* ring, uint32_t* cond,
+// Level of a draw against the nested thresholds, as the two ballot bits.
+__device__ __forceinline__ bool level_lo(uint32_t d, const FlipArgs& a) {
+    return (d < a.cmp1) ^ (d < a.cmp2) ^ (d < a.cmp3);
+}
+
+// One pass of colour c over stream t; the stream state is in B / st.  SLACK is
+// the free space of the MT19937 window (see mt_window).
+template <typename Word, int KIND, int SLACK>
+__device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t t, uint32_t* B, uint32_t* cond,
                                             StreamRegs& st, const StreamConst& k, int lane, int& dEsum) {
     constexpr int w = 8 * sizeof(Word);
     constexpr bool kMT = KIND == ISG_RNG_MT19937;
@@ -259,51 +271,44 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t t,
     for (int64_t g0 = r_begin; g0 < r_end; g0 += G) {
         const int nrows = (int)((r_end - g0) < G ? (r_end - g0) : G);
         const int D = nrows * half;
-        const int nquads = kMT ? (D >> 7) : 0;
-        for (int q = 0; q < nquads; ++q) {
-            uint32_t d[4], c4[4], c8[4], c12[4];
-            mt_quad(ring, st.iA, d, k.mul);
+        int b = 0;  // 32-draw blocks of this group done so far
+        if (kMT) {
+            const int nquads = D >> 7;
+            for (int q = 0; q < nquads; ++q) {
+                uint32_t d[4], lo[4], hi[4];
+                mt_quad<SLACK>(B, st.iA, st.pos, d, k.mul, lane);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                c4[j] = __ballot_sync(kFull, d[j] < a.cmp1);
-                c8[j] = __ballot_sync(kFull, d[j] < a.cmp2);
-                c12[j] = __ballot_sync(kFull, d[j] < a.cmp3);
+                for (int j = 0; j < 4; ++j) {
+                    lo[j] = __ballot_sync(kFull, level_lo(d[j], a));
+                    hi[j] = __ballot_sync(kFull, d[j] < a.cmp2);
+                }
+                if (lane == 0) {
+                    *(uint4*)(cond + 4 * q) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                    *(uint4*)(cond + kCondWords + 4 * q) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                }
             }
-            if (lane == 0) {
-                *(uint4*)(cond + 4 * q) = make_uint4(c4[0], c4[1], c4[2], c4[3]);
-                *(uint4*)(cond + kCondWords + 4 * q) = make_uint4(c8[0], c8[1], c8[2], c8[3]);
-                *(uint4*)(cond + 2 * kCondWords + 4 * q) = make_uint4(c12[0], c12[1], c12[2], c12[3]);
-            }
-        }
-        uint32_t* cw = cond + 4 * nquads;  // the pair and single steps continue the bit streams here
-        const int Dq = D - (nquads << 7);
-        const int npairs = Dq >> 6;
-        for (int q = 0; q < npairs; ++q) {
-            uint32_t dA, dB;
-            if (kMT) {
-                mt_pair(ring, st.iA, dA, dB, k.mul);
-            } else {
-                dA = st.xA;
-                dB = st.xB;
+            b = 4 * nquads;
+        } else {
+            const int npairs = D >> 6;
+            for (int q = 0; q < npairs; ++q) {
+                const uint32_t dA = st.xA, dB = st.xB;
                 st.xA = minstd_mulmod(st.xA, k.a64);
                 st.xB = minstd_mulmod(st.xB, k.a64);
+                const uint32_t loA = __ballot_sync(kFull, level_lo(dA, a));
+                const uint32_t loB = __ballot_sync(kFull, level_lo(dB, a));
+                const uint32_t hiA = __ballot_sync(kFull, dA < a.cmp2), hiB = __ballot_sync(kFull, dB < a.cmp2);
+                if (lane == 0) {
+                    *(uint2*)(cond + 2 * q) = make_uint2(loA, loB);
+                    *(uint2*)(cond + kCondWords + 2 * q) = make_uint2(hiA, hiB);
+                }
             }
-            const uint32_t A4 = __ballot_sync(kFull, dA < a.cmp1), B4 = __ballot_sync(kFull, dB < a.cmp1);
-            const uint32_t A8 = __ballot_sync(kFull, dA < a.cmp2), B8 = __ballot_sync(kFull, dB < a.cmp2);
-            const uint32_t A12 = __ballot_sync(kFull, dA < a.cmp3), B12 = __ballot_sync(kFull, dB < a.cmp3);
-            if (lane == 0) {
-                *(uint2*)(cw + 2 * q) = make_uint2(A4, B4);
-                *(uint2*)(cw + kCondWords + 2 * q) = make_uint2(A8, B8);
-                *(uint2*)(cw + 2 * kCondWords + 2 * q) = make_uint2(A12, B12);
-            }
+            b = 2 * npairs;
         }
-        int rem = Dq - (npairs << 6);
-        int b = 2 * npairs;
-        while (rem > 0) {
+        for (int rem = D - 32 * b; rem > 0; rem -= 32, ++b) {
             const int nvalid = rem < 32 ? rem : 32;
             uint32_t d;
             if (kMT) {
-                d = mt_single(ring, st.iA, lane, nvalid, k.mul);
+                d = mt_single<SLACK>(B, st.iA, st.pos, lane, nvalid, k.mul);
             } else {
                 d = st.xA;
                 const int src = lane + nvalid;
@@ -312,16 +317,12 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t t,
                 st.xA = src < 32 ? pa : pb;
                 st.xB = minstd_mulmod(st.xA, k.a32);
             }
-            const uint32_t m4 = __ballot_sync(kFull, d < a.cmp1);
-            const uint32_t m8 = __ballot_sync(kFull, d < a.cmp2);
-            const uint32_t m12 = __ballot_sync(kFull, d < a.cmp3);
+            const uint32_t lo = __ballot_sync(kFull, level_lo(d, a));
+            const uint32_t hi = __ballot_sync(kFull, d < a.cmp2);
             if (lane == 0) {
-                cw[b] = m4;
-                cw[kCondWords + b] = m8;
-                cw[2 * kCondWords + b] = m12;
+                cond[b] = lo;
+                cond[kCondWords + b] = hi;
             }
-            ++b;
-            rem -= nvalid;
         }
         __syncwarp();
         if (lane < nrows * W) word_update<Word>(a, c, r, y, z, lk, cond, loff, dEsum);
