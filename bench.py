@@ -17,6 +17,7 @@ barrier and the max-over-ranks timing ("replicas only", weak scaling).
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import math
@@ -53,6 +54,7 @@ def parse():
     p.add_argument("--plain-steps", type=int, default=300)
     p.add_argument("--batch-groups", type=int, default=2, help="timed 64-sweep groups of the batched workload (0: skip)")
     p.add_argument("--serve-jobs", type=int, default=16, help="jobs of the serving trace to serve (0: skip)")
+    p.add_argument("--L", type=int, default=0, help="lattice size instead of 1024 (quick runs and tests only)")
     return p.parse_args()
 
 
@@ -176,6 +178,17 @@ def traffic_from_profile(kind: str):
         return None
 
 
+def _stream_block(S: int, R: int, L: int, t0: int, m: int):
+    """Streams [t0, t1) of a lattice, restarting at 0 when fewer than m remain, and
+    the attempts of one colour pass over them (the last stream may be short)."""
+    t0 = t0 % S
+    if t0 + m > S:
+        t0 = 0
+    t1 = min(S, t0 + m)
+    rows = min(t1 * R, L * L) - t0 * R
+    return t0, t1, rows * (L // 2)
+
+
 def cpu_baseline(w, target_s: float = 12.0) -> dict:
     """The oracle, as it stands, on this host's cores: colour-pass pairs over a
     block of streams of the same lattice, repeated for about target_s seconds."""
@@ -184,15 +197,15 @@ def cpu_baseline(w, target_s: float = 12.0) -> dict:
     o = oracle.OracleSim(w.L, w.seed_J, w.seed_spin, w.beta, oracle.RNG_MT19937 if w.kind == "mt19937" else 0)
     S, R = oracle.num_streams(w.L), oracle.rows_per_stream(w.L)
     m = min(S, 4 * threads)
-    attempts_per_stream_pass = R * w.L // 2
     t_start = time.perf_counter()
     attempts = 0
     t0 = 0
     while time.perf_counter() - t_start < target_s:
-        o.pass_range(0, t0, t0 + m, threads)
-        o.pass_range(1, t0, t0 + m, threads)
-        attempts += 2 * m * attempts_per_stream_pass
-        t0 = (t0 + m) % S
+        t0, t1, n = _stream_block(S, R, w.L, t0, m)
+        o.pass_range(0, t0, t1, threads)
+        o.pass_range(1, t0, t1, threads)
+        attempts += 2 * n
+        t0 = t1
     dt = time.perf_counter() - t_start
     o.close()
     return {"value": dt * 1e12 / attempts, "unit": UNIT, "cores": min(threads, m), "kind": "oracle",
@@ -277,7 +290,7 @@ def run_ours(a, dist: Dist):
 
     torch.cuda.set_device(dist.local)
     isg.use_torch_allocator()
-    w = workloads.LARGE
+    w = workloads.LARGE if a.L <= 0 else dataclasses.replace(workloads.LARGE, L=a.L)
     seed_spin = w.seed_spin + 1000 * dist.rank
     sim = isg.Sim(w.L, w.seed_J, seed_spin, w.beta, w.kind)
     stream = torch.cuda.current_stream()
@@ -389,33 +402,35 @@ def run_reference(a, dist: Dist):
         return None
     import oracle
     from paper_1411_0127_gb300 import workloads
-    w = workloads.LARGE
+    w = workloads.LARGE if a.L <= 0 else dataclasses.replace(workloads.LARGE, L=a.L)
     threads = os.cpu_count() or 1
     o = oracle.OracleSim(w.L, w.seed_J, w.seed_spin, w.beta, oracle.RNG_MT19937)
     S, R = oracle.num_streams(w.L), oracle.rows_per_stream(w.L)
-    per_stream = R * w.L // 2
     t = time.perf_counter()
     o.pass_range(0, 0, threads, threads)
     o.pass_range(1, 0, threads, threads)
     cal = (time.perf_counter() - t) / threads            # seconds per stream pair, all cores busy
     budget = 60.0 / max(1, a.steps + a.warmup)
     m = int(max(threads, min(S, budget / max(cal, 1e-9))))
-    m = max(threads, m // threads * threads)
-    t0 = threads
+    m = min(S, max(threads, m // threads * threads))
+    t0 = threads % S
     for _ in range(a.warmup):
-        o.pass_range(0, t0 % S, t0 % S + m, threads)
-        o.pass_range(1, t0 % S, t0 % S + m, threads)
-        t0 += m
-    times = []
+        t0, t1, n = _stream_block(S, R, w.L, t0, m)
+        o.pass_range(0, t0, t1, threads)
+        o.pass_range(1, t0, t1, threads)
+        t0 = t1
+    times, done = [], 0
     for _ in range(a.steps):
+        t0, t1, n = _stream_block(S, R, w.L, t0, m)
         s = time.perf_counter()
-        o.pass_range(0, t0 % S, t0 % S + m, threads)
-        o.pass_range(1, t0 % S, t0 % S + m, threads)
+        o.pass_range(0, t0, t1, threads)
+        o.pass_range(1, t0, t1, threads)
         times.append(time.perf_counter() - s)
-        t0 += m
-    attempts = 2 * m * per_stream
+        done += 2 * n
+        t0 = t1
+    attempts = done // max(1, a.steps)
     total = sum(times)
-    value = total * 1e12 / (attempts * a.steps)
+    value = total * 1e12 / max(1, done)
     o.close()
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": a.steps,

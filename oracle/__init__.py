@@ -39,12 +39,20 @@ def build(force: bool = False) -> str:
 
 
 _lib = None
+_override = None   # path of another build of isg_oracle.c to bind instead (tests)
+
+
+def use_library(path):
+    """Bind the wrapper to another build of isg_oracle.c (None: the default build).
+    The mutation tests use this to check that the pins catch planted mistakes."""
+    global _lib, _override
+    _lib, _override = None, path
 
 
 def lib() -> ctypes.CDLL:
     global _lib
     if _lib is None:
-        L = ctypes.CDLL(build())
+        L = ctypes.CDLL(_override or build())
         u64, i64, i32, u32, dbl = (ctypes.c_uint64, ctypes.c_int64, ctypes.c_int,
                                    ctypes.c_uint32, ctypes.c_double)
         vp = ctypes.c_void_p

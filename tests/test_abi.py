@@ -64,6 +64,32 @@ def test_other_host_side_checks(isg):
     assert b"checkpoint" in lib.isg_last_error() or b"truncated" in lib.isg_last_error()
 
 
+def test_allocation_failure_is_reported(isg):
+    """An allocator that refuses: isg_create returns ISG_ERR_NOMEM, frees what it
+    got and touches no device (runs without a GPU)."""
+    lib = isg.lib()
+    calls = {"alloc": 0, "free": 0}
+
+    def refuse(size, ctx):
+        calls["alloc"] += 1
+        return None
+
+    def release(ptr, ctx):
+        calls["free"] += 1
+
+    a, f = isg._ALLOC_T(refuse), isg._FREE_T(release)
+    assert lib.isg_set_allocator(ctypes.cast(a, ctypes.c_void_p), ctypes.cast(f, ctypes.c_void_p), None) == isg.ISG_OK
+    try:
+        h = ctypes.c_void_p()
+        rc = lib.isg_create(64, 1, 2, 1.0, isg.ISG_RNG_MT19937, ctypes.byref(h))
+        assert rc == isg.ISG_ERR_NOMEM
+        assert h.value is None
+        assert b"allocation failed" in lib.isg_last_error()
+        assert calls["alloc"] >= 1 and calls["free"] == 0   # nothing was obtained, nothing to free
+    finally:
+        assert lib.isg_set_allocator(None, None, None) == isg.ISG_OK
+
+
 def test_binding_raises_with_message(isg):
     with pytest.raises(isg.IsgError) as ei:
         isg.Sim(7, 1, 2, 1.0, "minstd")
