@@ -55,6 +55,7 @@ def parse():
     p.add_argument("--batch-groups", type=int, default=2, help="timed 64-sweep groups of the batched workload (0: skip)")
     p.add_argument("--serve-jobs", type=int, default=16, help="jobs of the serving trace to serve (0: skip)")
     p.add_argument("--L", type=int, default=0, help="lattice size instead of 1024 (quick runs and tests only)")
+    p.add_argument("--other-configs", type=int, default=1, help="also time the L=32/256 and MINSTD lattices (0: skip)")
     return p.parse_args()
 
 
@@ -255,6 +256,30 @@ def batched_section(a, stream) -> dict:
     return out
 
 
+def other_configs_section(stream) -> dict:
+    """psFlip of the other single-lattice workloads (the parity configurations),
+    each timed with CUDA events after a warm-up, for context."""
+    import torch
+    import paper_1411_0127_gb300 as isg
+    from paper_1411_0127_gb300 import workloads
+    out = {}
+    cases = [("L32_minstd_T1.1", workloads.SMALL, 2000), ("L256_minstd_T0.7", workloads.MEDIUM_MINSTD, 1000),
+             ("L256_mt19937_T0.7", workloads.MEDIUM_MT, 1000),
+             ("L1024_minstd_T0.9", dataclasses.replace(workloads.LARGE, kind="minstd"), 300)]
+    for name, w, n in cases:
+        s = isg.Sim(w.L, w.seed_J, w.seed_spin, w.beta, w.kind)
+        s.sweep(10, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.sweep(n, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = {"psflip": e0.elapsed_time(e1) * 1e9 / (n * w.L ** 3), "sweeps": n,
+                     "streams": s.info()["streams"]}
+        s.close()
+    return out
+
+
 def serving_section(a) -> dict:
     """The first `--serve-jobs` jobs of the Poisson quench trace (200 jobs/s,
     L over even multiples of 16 in [32, 512], sweeps log-uniform in [1e2, 1e5],
@@ -351,6 +376,7 @@ def run_ours(a, dist: Dist):
 
     batched = batched_section(a, stream) if a.batch_groups > 0 else None
     serving = serving_section(a) if a.serve_jobs > 0 and dist.rank == 0 else None
+    others = other_configs_section(stream) if a.other_configs and dist.rank == 0 else None
 
     ops = OPS_PER_ATTEMPT[w.kind]
     achieved_tops = ops * attempts_per_launch / launch_s / 1e12
@@ -373,6 +399,7 @@ def run_ours(a, dist: Dist):
         "batched_psflip": batched["psflip"] if batched else None,
         "batched": batched,
         "serving": serving,
+        "other_configs": others,
         "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
                      "frac": achieved_tops / ALU_PEAK_TOPS, "traffic": traffic,
                      "kernel": "flip (one colour pass)", "ops_per_attempt": ops,
