@@ -94,13 +94,24 @@ template <int SLACK>
 __device__ __forceinline__ void mt_make_room(uint32_t* B, int& iA, int need, int lane) {
     if (iA + kMtN + need <= mt_window(SLACK)) return;
     __syncwarp();
-    uint32_t v[20];
+    if ((iA & 3) == 0) {  // 16-byte aligned: 156 four-word moves (5 per lane)
+        uint4 v[5];
 #pragma unroll
-    for (int q = 0; q < 20; ++q) v[q] = (lane + 32 * q < kMtN) ? B[iA + lane + 32 * q] : 0u;
-    __syncwarp();
+        for (int q = 0; q < 5; ++q)
+            if (lane + 32 * q < kMtN / 4) v[q] = *(const uint4*)(B + iA + 4 * (lane + 32 * q));
+        __syncwarp();
 #pragma unroll
-    for (int q = 0; q < 20; ++q)
-        if (lane + 32 * q < kMtN) B[lane + 32 * q] = v[q];
+        for (int q = 0; q < 5; ++q)
+            if (lane + 32 * q < kMtN / 4) *(uint4*)(B + 4 * (lane + 32 * q)) = v[q];
+    } else {
+        uint32_t v[20];
+#pragma unroll
+        for (int q = 0; q < 20; ++q) v[q] = (lane + 32 * q < kMtN) ? B[iA + lane + 32 * q] : 0u;
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 20; ++q)
+            if (lane + 32 * q < kMtN) B[lane + 32 * q] = v[q];
+    }
     __syncwarp();
     iA = 0;
 }
@@ -109,7 +120,7 @@ __device__ __forceinline__ void mt_make_room(uint32_t* B, int& iA, int need, int
 // which was appended 227 - 32j - l >= 100 draws before this step, so every
 // read of the step can precede every write (one warp barrier between).
 template <int SLACK>
-__device__ __forceinline__ void mt_quad(uint32_t* B, int& iA, int& pos, uint32_t d[4], const MtMul& k, int lane) {
+__device__ __forceinline__ void mt_quad(uint32_t* B, int& iA, uint32_t d[4], const MtMul& k, int lane) {
     mt_make_room<SLACK>(B, iA, 128, lane);
     uint32_t a[4], b[4], m[4];
 #pragma unroll
@@ -128,16 +139,13 @@ __device__ __forceinline__ void mt_quad(uint32_t* B, int& iA, int& pos, uint32_t
     }
     __syncwarp();
     iA += 128;
-    pos += 128;
-    pos = pos >= kMtN ? pos - kMtN : pos;
 #pragma unroll
     for (int j = 0; j < 4; ++j) d[j] = mt_temper_mul(d[j], k);
 }
 
 // One block of up to 32 draws (tail of a row group); lanes >= nvalid consume nothing.
 template <int SLACK>
-__device__ __forceinline__ uint32_t mt_single(uint32_t* B, int& iA, int& pos, int lane, int nvalid,
-                                              const MtMul& k) {
+__device__ __forceinline__ uint32_t mt_single(uint32_t* B, int& iA, int lane, int nvalid, const MtMul& k) {
     mt_make_room<SLACK>(B, iA, 32, lane);
     const int i = iA + lane;
     const uint32_t a = B[i], b = B[i + 1], m = B[i + kMtM];
@@ -146,8 +154,6 @@ __device__ __forceinline__ uint32_t mt_single(uint32_t* B, int& iA, int& pos, in
     if (lane < nvalid) B[i + kMtN] = v;
     __syncwarp();
     iA += nvalid;
-    pos += nvalid;
-    pos = pos >= kMtN ? pos - kMtN : pos;
     return mt_temper_mul(v, k);
 }
 
@@ -271,12 +277,13 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t t,
     for (int64_t g0 = r_begin; g0 < r_end; g0 += G) {
         const int nrows = (int)((r_end - g0) < G ? (r_end - g0) : G);
         const int D = nrows * half;
+        if (kMT) st.pos = (st.pos + D) % kMtN;  // the ring position after this group's draws
         int b = 0;  // 32-draw blocks of this group done so far
         if (kMT) {
             const int nquads = D >> 7;
             for (int q = 0; q < nquads; ++q) {
                 uint32_t d[4], lo[4], hi[4];
-                mt_quad<SLACK>(B, st.iA, st.pos, d, k.mul, lane);
+                mt_quad<SLACK>(B, st.iA, d, k.mul, lane);
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     lo[j] = __ballot_sync(kFull, level_lo(d[j], a));
@@ -308,7 +315,7 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t t,
             const int nvalid = rem < 32 ? rem : 32;
             uint32_t d;
             if (kMT) {
-                d = mt_single<SLACK>(B, st.iA, st.pos, lane, nvalid, k.mul);
+                d = mt_single<SLACK>(B, st.iA, lane, nvalid, k.mul);
             } else {
                 d = st.xA;
                 const int src = lane + nvalid;
