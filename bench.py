@@ -280,6 +280,24 @@ def other_configs_section(stream) -> dict:
     return out
 
 
+def rng_section() -> dict:
+    """Device-API generator benchmark (Sec. 3, Table MYTEST): the paper's run is
+    64 x 256 threads x 2^15 numbers x 10 = 5.4e9 instances; here 8192 streams x
+    2^16 numbers x 10 calls (the same total), counting odd outputs."""
+    import paper_1411_0127_gb300 as isg
+    out = {"paper_gtx_titan_instances_per_s": {"mt19937": 14.1e9, "minstd": 8.9e10}}
+    for kind in ("mt19937", "minstd"):
+        isg.rng_count_odd(kind, 1, 8192, 4096)                 # warm-up
+        total_ms, odd, n = 0.0, 0, 0
+        for rep in range(10):
+            o, ms = isg.rng_count_odd(kind, 100 + rep, 8192, 2**16)
+            total_ms += ms
+            odd += o
+            n += 8192 * 2**16
+        out[kind] = {"instances_per_s": n / (total_ms / 1e3), "odd_fraction": odd / n, "instances": n}
+    return out
+
+
 def serving_section(a) -> dict:
     """The first `--serve-jobs` jobs of the Poisson quench trace (200 jobs/s,
     L over even multiples of 16 in [32, 512], sweeps log-uniform in [1e2, 1e5],
@@ -377,6 +395,7 @@ def run_ours(a, dist: Dist):
     batched = batched_section(a, stream) if a.batch_groups > 0 else None
     serving = serving_section(a) if a.serve_jobs > 0 and dist.rank == 0 else None
     others = other_configs_section(stream) if a.other_configs and dist.rank == 0 else None
+    rng = rng_section() if a.other_configs and dist.rank == 0 else None
 
     ops = OPS_PER_ATTEMPT[w.kind]
     achieved_tops = ops * attempts_per_launch / launch_s / 1e12
@@ -400,6 +419,7 @@ def run_ours(a, dist: Dist):
         "batched": batched,
         "serving": serving,
         "other_configs": others,
+        "rng_device_api": rng,
         "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
                      "frac": achieved_tops / ALU_PEAK_TOPS, "traffic": traffic,
                      "kernel": "flip (one colour pass)", "ops_per_attempt": ops,

@@ -221,6 +221,17 @@ int isg_server_job(const isg_server *s, int64_t id, int *status, int64_t *E, uin
 int isg_server_stats(const isg_server *s, int64_t *iterations, int64_t *attempts, double *wall_s, double *busy_s,
                      int *peak_active, size_t *peak_bytes);
 
+/* ----------------------------------------------------------- benchmark --- */
+
+/* Device-API generator benchmark of Sec. 3 (Table MYTEST: produce numbers on
+ * the device and count the odd ones).  `streams` streams of rng_kind, seeded as
+ * the streams of a lattice with seed_spin = seed, each produce n consecutive
+ * raw outputs (MT19937: the tempered word; MINSTD: the state x) with the warp
+ * engines of the flip kernels.  Sync; *odd = number of odd outputs, *gen_ms
+ * (may be NULL) = device time of the generation kernel alone.  Allocates its
+ * own temporary buffers. */
+int isg_rng_count_odd(int rng_kind, uint64_t seed, int64_t streams, int64_t n, uint64_t *odd, double *gen_ms);
+
 /* ------------------------------------------------------- no allocation --- */
 
 /* The energy of Eq. 1, like isg_energy, for callers that must not allocate

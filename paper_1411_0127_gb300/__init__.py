@@ -63,7 +63,18 @@ SIGNATURES = {
     "isg_server_run": (_i32, [_vp, _dbl]),
     "isg_server_job": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
     "isg_server_stats": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "isg_rng_count_odd": (_i32, [_i32, _u64, _i64, _i64, _vp, _vp]),
 }
+
+
+def rng_count_odd(rng_kind, seed: int, streams: int, n: int):
+    """Odd raw outputs of `streams` generator streams of n numbers each, and the
+    generation kernel's device time in ms (see isg_rng_count_odd)."""
+    kind = RNG_KINDS[rng_kind] if isinstance(rng_kind, str) else int(rng_kind)
+    odd, ms = ctypes.c_uint64(), ctypes.c_double()
+    _check(lib().isg_rng_count_odd(kind, int(seed) & (2**64 - 1), int(streams), int(n), ctypes.byref(odd),
+                                   ctypes.byref(ms)))
+    return odd.value, ms.value
 
 
 class IsgError(RuntimeError):

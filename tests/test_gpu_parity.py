@@ -76,6 +76,23 @@ def test_stream_draws(isg, kind):
         assert np.array_equal(g.peek_draws(t, 777), o.peek_draws(t, 777))
 
 
+@pytest.mark.parametrize("kind", ["minstd", "mt19937"])
+@pytest.mark.parametrize("n", [1000, 4096, 20001])
+def test_generator_benchmark_counts(isg, kind, n):
+    """The device-API benchmark (odd outputs) against the oracle's generators,
+    seeded like lattice streams: counts must be equal."""
+    seed, streams = 77, 5
+    odd, ms = isg.rng_count_odd(kind, seed, streams, n)
+    ref = 0
+    for t in range(streams):
+        v = oracle.splitmix64(seed ^ K_STREAMS, t)
+        out = (oracle.mt19937_outputs(v & 0xFFFFFFFF, n) if kind == "mt19937"
+               else oracle.minstd_outputs(1 + v % (2**31 - 2), n))
+        ref += int((out & 1).sum())
+    assert odd == ref
+    assert ms >= 0.0
+
+
 # ------------------------------------------------------------------- init ---
 
 @pytest.mark.parametrize("L", [4, 6, 16, 32, 48, 96, 130])
