@@ -65,6 +65,13 @@ typedef struct isg_batch isg_batch;
 int isg_create(int L, uint64_t seed_J, uint64_t seed_spin, double beta, int rng_kind,
                isg_sim **out);
 
+/* As isg_create, but the RNG streams are seeded from seed_rng instead of
+ * seed_spin.  Sec. 4's asynchronous multispin coding shares one draw per site
+ * among the samples of a word; each of those samples follows exactly the
+ * trajectory of an isg_create2 handle with the common seed_rng. */
+int isg_create2(int L, uint64_t seed_J, uint64_t seed_spin, uint64_t seed_rng, double beta, int rng_kind,
+                isg_sim **out);
+
 /* Free every device buffer of the handle (NULL is ignored). */
 void isg_destroy(isg_sim *h);
 

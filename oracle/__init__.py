@@ -66,6 +66,7 @@ def lib() -> ctypes.CDLL:
             "or_unsatisfied": (i32, [ctypes.c_int8, vp, vp]),
             "or_accept": (i32, [i32, u32, vp]),
             "or_create": (vp, [i32, u64, u64, dbl, i32]),
+            "or_create2": (vp, [i32, u64, u64, u64, dbl, i32]),
             "or_destroy": (None, [vp]),
             "or_sweep": (None, [vp, i64, i32]),
             "or_energy": (i64, [vp]),
@@ -146,8 +147,11 @@ def accept(u: int, d: int, thr: np.ndarray) -> bool:
 class OracleSim:
     """One lattice with its coupling sample, spins and RNG streams."""
 
-    def __init__(self, L: int, seed_J: int, seed_spin: int, beta: float, kind: int):
-        self._h = lib().or_create(L, seed_J, seed_spin, float(beta), kind)
+    def __init__(self, L: int, seed_J: int, seed_spin: int, beta: float, kind: int, seed_rng: int = None):
+        if seed_rng is None:
+            self._h = lib().or_create(L, seed_J, seed_spin, float(beta), kind)
+        else:
+            self._h = lib().or_create2(L, seed_J, seed_spin, seed_rng, float(beta), kind)
         if not self._h:
             raise ValueError("oracle: invalid arguments L=%r beta=%r kind=%r" % (L, beta, kind))
         self.L, self.N, self.kind, self.beta = L, L ** 3, kind, beta

@@ -178,6 +178,11 @@ static inline int64_t idx(int L, int x, int y, int z)
 
 or_sim *or_create(int L, uint64_t seed_J, uint64_t seed_spin, double beta, int kind)
 {
+    return or_create2(L, seed_J, seed_spin, seed_spin, beta, kind);
+}
+
+or_sim *or_create2(int L, uint64_t seed_J, uint64_t seed_spin, uint64_t seed_rng, double beta, int kind)
+{
     if (L < 4 || (L & 1) || L > 2048) return NULL;
     if (!(beta > 0.0)) return NULL; /* rejects 0, negatives and NaN; +inf allowed */
     if (kind != OR_RNG_MINSTD && kind != OR_RNG_MT19937) return NULL;
@@ -203,7 +208,7 @@ or_sim *or_create(int L, uint64_t seed_J, uint64_t seed_spin, double beta, int k
         o->s[i] = (or_splitmix64(seed_spin ^ SALT_SPINS, (uint64_t)i) >> 63) ? -1 : 1;
     }
     for (int64_t t = 0; t < o->S; ++t) {
-        uint64_t v = or_splitmix64(seed_spin ^ SALT_STREAMS, (uint64_t)t);
+        uint64_t v = or_splitmix64(seed_rng ^ SALT_STREAMS, (uint64_t)t);
         o->st[t].kind = kind;
         if (kind == OR_RNG_MT19937) mt_seed(&o->st[t].mt, (uint32_t)v);
         else o->st[t].minstd = 1u + (uint32_t)(v % 2147483646u);

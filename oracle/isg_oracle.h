@@ -55,6 +55,12 @@ int or_accept(int u, uint32_t d, const uint32_t thr[4]);
 /* Simulator.  Returns NULL on a bad argument (L odd, L < 4, bad kind, beta <= 0
  * or NaN) or out of memory. */
 or_sim *or_create(int L, uint64_t seed_J, uint64_t seed_spin, double beta, int kind);
+/* The same with the RNG streams seeded from seed_rng instead of seed_spin.
+ * Sec. 4's asynchronous multispin coding runs 32 samples on one shared draw per
+ * site: sample b of such a word follows exactly the trajectory of
+ * or_create2(L, seed_J_b, seed_spin_b, seed_rng, ...), because every attempt
+ * consumes one draw whatever its outcome (Reading 4). */
+or_sim *or_create2(int L, uint64_t seed_J, uint64_t seed_spin, uint64_t seed_rng, double beta, int kind);
 void    or_destroy(or_sim *s);
 /* n full sweeps (red then blue) using up to nthreads threads; the result does
  * not depend on nthreads. */

@@ -30,6 +30,7 @@ _PP = ctypes.POINTER(ctypes.c_void_p)
 # name -> (restype, argtypes); every name here is declared in include/isg.h
 SIGNATURES = {
     "isg_create": (_i32, [_i32, _u64, _u64, _dbl, _i32, _PP]),
+    "isg_create2": (_i32, [_i32, _u64, _u64, _u64, _dbl, _i32, _PP]),
     "isg_destroy": (None, [_vp]),
     "isg_set_allocator": (_i32, [_vp, _vp, _vp]),
     "isg_last_error": (ctypes.c_char_p, []),
@@ -160,12 +161,17 @@ def use_default_allocator():
 class Sim:
     """One L^3 lattice (one replica): couplings, bit-packed spins, RNG streams."""
 
-    def __init__(self, L: int, seed_J: int, seed_spin: int, beta: float, rng_kind="minstd", *, _handle=None):
+    def __init__(self, L: int, seed_J: int, seed_spin: int, beta: float, rng_kind="minstd", *, seed_rng=None,
+                 _handle=None):
         kind = RNG_KINDS[rng_kind] if isinstance(rng_kind, str) else int(rng_kind)
         if _handle is None:
             h = ctypes.c_void_p()
-            _check(lib().isg_create(int(L), int(seed_J) & (2**64 - 1), int(seed_spin) & (2**64 - 1),
-                                    float(beta), kind, ctypes.byref(h)))
+            if seed_rng is None:
+                _check(lib().isg_create(int(L), int(seed_J) & (2**64 - 1), int(seed_spin) & (2**64 - 1),
+                                        float(beta), kind, ctypes.byref(h)))
+            else:
+                _check(lib().isg_create2(int(L), int(seed_J) & (2**64 - 1), int(seed_spin) & (2**64 - 1),
+                                         int(seed_rng) & (2**64 - 1), float(beta), kind, ctypes.byref(h)))
             _handle = h.value
         self._h = _handle
         self.L, self.N, self.kind, self.beta = int(L), int(L) ** 3, kind, float(beta)

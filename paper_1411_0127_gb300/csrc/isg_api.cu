@@ -132,7 +132,7 @@ static int restart_tracking(isg_sim* h, cudaStream_t s) {
     return e == cudaSuccess ? ISG_OK : cuda_fail(e, "reset tracked energy");
 }
 
-int create_sim(int L, uint64_t seed_J, uint64_t seed_spin, double beta, int rng_kind, bool force32,
+int create_sim(int L, uint64_t seed_J, uint64_t seed_spin, uint64_t seed_rng, double beta, int rng_kind, bool force32,
                isg_sim** out) {
     if (!out) { set_error("isg_create: out is NULL"); return ISG_ERR_ARG; }
     *out = nullptr;
@@ -149,6 +149,7 @@ int create_sim(int L, uint64_t seed_J, uint64_t seed_spin, double beta, int rng_
     h->beta = beta;
     h->seed_J = seed_J;
     h->seed_spin = seed_spin;
+    h->seed_rng = seed_rng;
     h->force32 = force32;
     thresholds(beta, h->thr);
     int rc = alloc_sim(h);
@@ -199,7 +200,12 @@ int isg_set_allocator(void* (*alloc)(size_t, void*), void (*free_fn)(void*, void
 }
 
 int isg_create(int L, uint64_t seed_J, uint64_t seed_spin, double beta, int rng_kind, isg_sim** out) {
-    return create_sim(L, seed_J, seed_spin, beta, rng_kind, false, out);
+    return create_sim(L, seed_J, seed_spin, seed_spin, beta, rng_kind, false, out);
+}
+
+int isg_create2(int L, uint64_t seed_J, uint64_t seed_spin, uint64_t seed_rng, double beta, int rng_kind,
+                isg_sim** out) {
+    return create_sim(L, seed_J, seed_spin, seed_rng, beta, rng_kind, false, out);
 }
 
 void isg_destroy(isg_sim* h) {
@@ -363,11 +369,11 @@ struct SaveHeader {
     char magic[8];
     uint32_t version, L, kind, wbits;
     double beta;
-    uint64_t seed_J, seed_spin;
+    uint64_t seed_J, seed_spin, seed_rng;
     int64_t R, S, sweeps, E0, dE, plane_bytes, rng_words;
 };
 
-static const char kMagic[8] = {'I', 'S', 'G', 'C', 'K', 'P', 'T', '1'};
+static const char kMagic[8] = {'I', 'S', 'G', 'C', 'K', 'P', 'T', '2'};
 
 int isg_save(const isg_sim* h, void* buf, size_t* n, void* stream) {
     if (!h || !n) { set_error("isg_save: NULL argument"); return ISG_ERR_ARG; }
@@ -386,6 +392,7 @@ int isg_save(const isg_sim* h, void* buf, size_t* n, void* stream) {
     hd.beta = h->beta;
     hd.seed_J = h->seed_J;
     hd.seed_spin = h->seed_spin;
+    hd.seed_rng = h->seed_rng;
     hd.R = h->R;
     hd.S = h->S;
     hd.sweeps = h->sweeps;
@@ -427,6 +434,7 @@ int isg_load(const void* buf, size_t n, isg_sim** out) {
     h->beta = hd.beta;
     h->seed_J = hd.seed_J;
     h->seed_spin = hd.seed_spin;
+    h->seed_rng = hd.seed_rng;
     h->force32 = hd.wbits == 32;
     thresholds(h->beta, h->thr);
     int rc = alloc_sim(h);

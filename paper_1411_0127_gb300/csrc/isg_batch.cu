@@ -246,7 +246,7 @@ int isg_batch_create(int n, const int* L, const uint64_t* seed_J, const uint64_t
     b->reps.assign(2 * n, nullptr);
     for (int r = 0; r < 2 * n; ++r) {
         const int s = r / 2;
-        const int rc = create_sim(L[s], seed_J[s], seed_spin[r], beta[s], rng_kind, true, &b->reps[r]);
+        const int rc = create_sim(L[s], seed_J[s], seed_spin[r], seed_spin[r], beta[s], rng_kind, true, &b->reps[r]);
         if (rc) { batch_free(b); return rc; }
         b->attempts_per_sweep += (int64_t)L[s] * L[s] * L[s];
     }

@@ -193,7 +193,7 @@ struct isg_sim {
     int kind = 0;
     double beta = 0.0;
     uint32_t thr[4] = {0, 0, 0, 0};
-    uint64_t seed_J = 0, seed_spin = 0;
+    uint64_t seed_J = 0, seed_spin = 0, seed_rng = 0;  // seed_rng seeds the RNG streams
     int64_t rows = 0, R = 0, S = 0;
     int64_t plane_bytes = 0;            // one plane: rows * W * wbits / 8
     unsigned char* planes = nullptr;    // 8 planes: index 4*c + q, q = S, Jx, Jy, Jz
@@ -217,7 +217,7 @@ void set_error(const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
 void* dev_alloc(isg_sim* h, size_t n);
 void dev_free(isg_sim* h, void* p);
-int create_sim(int L, uint64_t seed_J, uint64_t seed_spin, double beta, int rng_kind, bool force32,
+int create_sim(int L, uint64_t seed_J, uint64_t seed_spin, uint64_t seed_rng, double beta, int rng_kind, bool force32,
                isg_sim** out);
 void destroy_sim(isg_sim* h);
 size_t sim_device_bytes(int L, int rng_kind, bool force32);

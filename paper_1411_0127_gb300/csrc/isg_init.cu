@@ -2,7 +2,8 @@
 //
 // Couplings (Eq. 2): J_d(i) = -1 when bit 63 of SplitMix64(seed_J ^ K_J, 3i + d)
 // is set; spins: s_i = -1 when bit 63 of SplitMix64(seed_spin ^ K_S, i) is set.
-// Streams: v_t = SplitMix64(seed_spin ^ K_R, t); MT19937 starts from
+// Streams: v_t = SplitMix64(seed_rng ^ K_R, t) (seed_rng = seed_spin unless the
+// handle was made with isg_create2); MT19937 starts from
 // init_genrand((uint32) v_t), MINSTD from x_0 = 1 + v_t mod (2^31 - 2) (Sec. 3).
 #include "isg_common.cuh"
 
@@ -77,10 +78,10 @@ cudaError_t launch_init_planes(isg_sim* h, cudaStream_t s) {
 }
 
 // One thread per stream.
-__global__ void init_rng_kernel(int kind, uint64_t seed_spin, int64_t S, uint32_t* rng, uint32_t* pos) {
+__global__ void init_rng_kernel(int kind, uint64_t seed_rng, int64_t S, uint32_t* rng, uint32_t* pos) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= S) return;
-    const uint64_t v = splitmix64(seed_spin ^ kSaltStreams, (uint64_t)t);
+    const uint64_t v = splitmix64(seed_rng ^ kSaltStreams, (uint64_t)t);
     if (kind == ISG_RNG_MT19937) {
         uint32_t* x = rng + t * kMtN;
         uint32_t prev = (uint32_t)v;
@@ -98,7 +99,7 @@ __global__ void init_rng_kernel(int kind, uint64_t seed_spin, int64_t S, uint32_
 cudaError_t launch_init_rng(isg_sim* h, cudaStream_t s) {
     const int threads = 128;
     const unsigned blocks = (unsigned)((h->S + threads - 1) / threads);
-    init_rng_kernel<<<blocks, threads, 0, s>>>(h->kind, h->seed_spin, h->S, h->rng, h->rng_pos);
+    init_rng_kernel<<<blocks, threads, 0, s>>>(h->kind, h->seed_rng, h->S, h->rng, h->rng_pos);
     return cudaGetLastError();
 }
 

@@ -85,7 +85,7 @@ extern "C" int isg_rng_count_odd(int rng_kind, uint64_t seed, int64_t streams, i
     if (e == cudaSuccess) {
         isg_sim tmp;  // only the fields the seeding kernel reads
         tmp.kind = rng_kind;
-        tmp.seed_spin = seed;
+        tmp.seed_rng = seed;
         tmp.S = streams;
         tmp.rng = state;
         tmp.rng_pos = pos;

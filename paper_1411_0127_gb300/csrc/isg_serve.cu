@@ -287,7 +287,7 @@ int isg_server_run(isg_server* s, double time_limit_s) {
         while (next < order.size()) {
             ServeJob& J = s->jobs[order[next]];
             if (J.arrival > now || used + J.bytes > s->budget || (int)active.size() >= s->max_active) break;
-            const int rc = create_sim(J.L, J.seed_J, J.seed_spin, J.beta, J.kind, !J.wide, &J.h);
+            const int rc = create_sim(J.L, J.seed_J, J.seed_spin, J.seed_spin, J.beta, J.kind, !J.wide, &J.h);
             ++next;
             if (rc) {
                 J.status = rc;
