@@ -56,6 +56,7 @@ def parse():
     p.add_argument("--serve-jobs", type=int, default=16, help="jobs of the serving trace to serve (0: skip)")
     p.add_argument("--L", type=int, default=0, help="lattice size instead of 1024 (quick runs and tests only)")
     p.add_argument("--other-configs", type=int, default=1, help="also time the L=32/256 and MINSTD lattices (0: skip)")
+    p.add_argument("--amsc", type=int, default=1, help="also time the asynchronous multispin ensembles (0: skip)")
     return p.parse_args()
 
 
@@ -298,6 +299,33 @@ def rng_section() -> dict:
     return out
 
 
+def amsc_section(stream) -> dict:
+    """Asynchronous multispin coding (Sec. 4): 32 systems per word, one draw per
+    site shared by the 32.  psFlip = time / (32 L^3 sweeps), the paper's unit for
+    its ~3 (MINSTD) and ~5 (MT19937) psFlip on a GTX Titan.  Algorithmic HBM
+    bytes per colour pass and site word: 8 words read (S, Jx, Jy, Jz of both
+    colours) + 1 written = 36 B per 32 attempts."""
+    import torch
+    import paper_1411_0127_gb300 as isg
+    from paper_1411_0127_gb300 import workloads
+    out = {"paper_gtx_titan_psflip": {"minstd": 3.0, "mt19937": 5.0}, "bytes_per_attempt": 36 / 32}
+    for L, kind, n in [(1024, "mt19937", 40), (1024, "minstd", 40), (256, "mt19937", 400)]:
+        seed_J, seed_spin = workloads.amsc_seeds(L)
+        m = isg.Amsc(L, seed_J, seed_spin, 12345, 1 / 0.9, kind)
+        m.sweep(3, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        m.sweep(n, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        att = 32 * L ** 3 * n
+        out["L%d_%s_T0.9" % (L, kind)] = {"psflip": ms * 1e9 / att, "sweeps": n,
+                                          "hbm_gbs": att * 36 / 32 / (ms / 1e3) / 1e9}
+        m.close()
+    return out
+
+
 def serving_section(a) -> dict:
     """The first `--serve-jobs` jobs of the Poisson quench trace (200 jobs/s,
     L over even multiples of 16 in [32, 512], sweeps log-uniform in [1e2, 1e5],
@@ -396,6 +424,7 @@ def run_ours(a, dist: Dist):
     serving = serving_section(a) if a.serve_jobs > 0 and dist.rank == 0 else None
     others = other_configs_section(stream) if a.other_configs and dist.rank == 0 else None
     rng = rng_section() if a.other_configs and dist.rank == 0 else None
+    amsc = amsc_section(stream) if a.amsc and dist.rank == 0 else None
 
     ops = OPS_PER_ATTEMPT[w.kind]
     achieved_tops = ops * attempts_per_launch / launch_s / 1e12
@@ -420,6 +449,7 @@ def run_ours(a, dist: Dist):
         "serving": serving,
         "other_configs": others,
         "rng_device_api": rng,
+        "amsc": amsc,
         "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
                      "frac": achieved_tops / ALU_PEAK_TOPS, "traffic": traffic,
                      "kernel": "flip (one colour pass)", "ops_per_attempt": ops,

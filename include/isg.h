@@ -228,6 +228,40 @@ int isg_server_job(const isg_server *s, int64_t id, int *status, int64_t *E, uin
 int isg_server_stats(const isg_server *s, int64_t *iterations, int64_t *attempts, double *wall_s, double *busy_s,
                      int *peak_active, size_t *peak_bytes);
 
+/* ---------------------------------------------- asynchronous multispin --- */
+
+/* Asynchronous multispin coding (Sec. 4): 32 systems of the same size L share
+ * every word, bit b of the word at a site belonging to system b, and ONE draw
+ * per site serves all 32 (the paper's cond masks are all ones or all zeros).
+ * System b has couplings from seed_J[b] and spins from seed_spin[b] (arrays of
+ * 32); the draws come from streams seeded by seed_rng, with the stream
+ * partition and site -> (stream, draw) map of a single lattice.  Hence system b
+ * follows, bit for bit, the trajectory of
+ * isg_create2(L, seed_J[b], seed_spin[b], seed_rng, beta, rng_kind): the 32
+ * systems are correlated through their shared draws, as the paper notes.
+ * L even, 4 <= L <= 1024; beta > 0.  Device memory: 8 planes of L^3/2 words
+ * (4 L^3 bytes) plus the streams, from cudaMalloc.  Sync; ISG_ERR_ARG on a bad
+ * argument (nothing allocated), ISG_ERR_CUDA on a device error. */
+typedef struct isg_amsc isg_amsc;
+int isg_amsc_create(int L, const uint64_t *seed_J, const uint64_t *seed_spin, uint64_t seed_rng, double beta,
+                    int rng_kind, isg_amsc **out);
+
+/* Free the ensemble (NULL is ignored; synchronises the device first). */
+void isg_amsc_destroy(isg_amsc *m);
+
+/* Enqueue n sweeps of all 32 systems on cuda_stream (async): per colour one
+ * persistent launch in which a warp takes stream after stream and each lane
+ * updates one site word with its own draw.  ISG_ERR_ARG for n < 0. */
+int isg_amsc_sweep(isg_amsc *m, int64_t n, void *cuda_stream);
+
+/* Energies E[b] = -sum J s s' of the 32 systems (Eq. 1), counted bit-parallel
+ * on the device (sync on cuda_stream).  E must hold 32 entries. */
+int isg_amsc_energies(isg_amsc *m, int64_t *E, void *cuda_stream);
+
+/* Spins of system `sample` (0..31) as +-1 in site order i = x + L y + L^2 z
+ * into host_out (n >= L^3; sync).  Uses an L^3-byte temporary device buffer. */
+int isg_amsc_read_spins(const isg_amsc *m, int sample, int8_t *host_out, size_t n, void *cuda_stream);
+
 /* ----------------------------------------------------------- benchmark --- */
 
 /* Device-API generator benchmark of Sec. 3 (Table MYTEST: produce numbers on

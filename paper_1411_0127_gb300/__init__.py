@@ -65,6 +65,11 @@ SIGNATURES = {
     "isg_server_job": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
     "isg_server_stats": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "isg_rng_count_odd": (_i32, [_i32, _u64, _i64, _i64, _vp, _vp]),
+    "isg_amsc_create": (_i32, [_i32, _vp, _vp, _u64, _dbl, _i32, _PP]),
+    "isg_amsc_destroy": (None, [_vp]),
+    "isg_amsc_sweep": (_i32, [_vp, _i64, _vp]),
+    "isg_amsc_energies": (_i32, [_vp, _vp, _vp]),
+    "isg_amsc_read_spins": (_i32, [_vp, _i32, _vp, _sz, _vp]),
 }
 
 
@@ -351,6 +356,50 @@ class Batch:
         H = np.empty(2 * self.n, dtype=np.uint64)
         _check(lib().isg_batch_tracked(self._h, _ptr(E), _ptr(H), _stream(stream)))
         return E, H
+
+
+class Amsc:
+    """32 systems of one size in asynchronous multispin coding (one shared draw
+    per site); system b follows Sim(L, seed_J[b], seed_spin[b], beta, kind,
+    seed_rng=seed_rng) bit for bit."""
+
+    SAMPLES = 32
+
+    def __init__(self, L: int, seed_J, seed_spin, seed_rng: int, beta: float, rng_kind="mt19937"):
+        kind = RNG_KINDS[rng_kind] if isinstance(rng_kind, str) else int(rng_kind)
+        J = np.ascontiguousarray([int(v) & (2**64 - 1) for v in seed_J], dtype=np.uint64)
+        S = np.ascontiguousarray([int(v) & (2**64 - 1) for v in seed_spin], dtype=np.uint64)
+        if J.size != self.SAMPLES or S.size != self.SAMPLES:
+            raise ValueError("Amsc needs 32 coupling seeds and 32 spin seeds")
+        h = ctypes.c_void_p()
+        _check(lib().isg_amsc_create(int(L), _ptr(J), _ptr(S), int(seed_rng) & (2**64 - 1), float(beta), kind,
+                                     ctypes.byref(h)))
+        self._h = h.value
+        self.L, self.N, self.kind, self.beta = int(L), int(L) ** 3, kind, float(beta)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().isg_amsc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sweep(self, n: int = 1, stream=None):
+        _check(lib().isg_amsc_sweep(self._h, int(n), _stream(stream)))
+
+    def energies(self, stream=None) -> np.ndarray:
+        E = np.empty(self.SAMPLES, dtype=np.int64)
+        _check(lib().isg_amsc_energies(self._h, _ptr(E), _stream(stream)))
+        return E
+
+    def spins(self, sample: int, stream=None) -> np.ndarray:
+        out = np.empty(self.N, dtype=np.int8)
+        _check(lib().isg_amsc_read_spins(self._h, int(sample), _ptr(out), out.size, _stream(stream)))
+        return out
 
 
 class Server:

@@ -1,0 +1,448 @@
+// isg_amsc.cu -- asynchronous multispin coding (Sec. 4): 32 disorder samples of
+// one size L stored bit-parallel, bit b of every word belonging to sample b,
+// all updated with ONE shared draw per site.
+//
+// The paper's scheme: the spins of different samples at the same vertex share a
+// word, and one random number serves the whole word: cond_k = -(R < EXP_k) is
+// all ones or all zeros (Sec. 4), and the mask is applied with one XOR.  Here:
+//   * planes: per colour c, S_c, Jx_c, Jy_c, Jz_c, one 32-bit word per site of
+//     that colour, row r = y + L*z holding the L/2 sites x = 2h + ((c+y+z) & 1)
+//     at words r*(L/2) + h;
+//   * draws: the map of the single-sample engine (Sec. 2 of DESIGN: streams of
+//     R(L) rows, sites visited in row order and ascending x, one draw per site
+//     and colour pass), seeded from seed_rng; so sample b follows exactly the
+//     trajectory of a lone lattice with (seed_J[b], seed_spin[b], seed_rng);
+//   * one lane updates one site: it takes its own draw, loads the site word and
+//     the twelve neighbour and coupling words, counts unsatisfied bonds of the 32
+//     samples with the bit-sliced adder, and flips with the broadcast masks.
+#include <new>
+
+#include "isg_stream.cuh"
+
+struct isg_amsc {
+    int L = 0, half = 0, kind = 0;
+    double beta = 0.0;
+    uint32_t thr[4] = {0, 0, 0, 0};
+    uint64_t seed_rng = 0;
+    uint64_t seed_J[32] = {}, seed_spin[32] = {};
+    int64_t rows = 0, R = 0, S = 0, plane_words = 0;
+    uint32_t* planes = nullptr;         // 8 planes of plane_words words: index 4*c + q
+    uint32_t* rng = nullptr;
+    uint32_t* rng_pos = nullptr;
+    unsigned long long* ctr = nullptr;  // [0] stream tickets, [1..32] energy counters
+    unsigned long long tickets = 0;
+    int64_t sweeps = 0;
+};
+
+namespace isg {
+
+constexpr int kAmscWarps = 4;
+constexpr int kAmscSlack = 1024;
+
+struct AmscArgs {
+    uint32_t* planes;
+    int64_t plane_words;
+    int L, half, c;
+    int64_t R, S, rows;
+    uint32_t cmp1, cmp2, cmp3;
+};
+
+struct AmscSeeds {
+    uint64_t J[32], S[32];
+};
+
+// One site word of colour c at row r = y + L z, position h.
+__device__ __forceinline__ void amsc_site(const AmscArgs& a, int r, int y, int z, int h, uint32_t d) {
+    const int L = a.L, half = a.half, c = a.c, n = c ^ 1;
+    const int64_t pw = a.plane_words;
+    uint32_t* Sc = a.planes + (4 * c) * pw;
+    const uint32_t* Jxc = a.planes + (4 * c + 1) * pw;
+    const uint32_t* Jyc = a.planes + (4 * c + 2) * pw;
+    const uint32_t* Jzc = a.planes + (4 * c + 3) * pw;
+    const uint32_t* Sn = a.planes + (4 * n) * pw;
+    const uint32_t* Jxn = a.planes + (4 * n + 1) * pw;
+    const uint32_t* Jyn = a.planes + (4 * n + 2) * pw;
+    const uint32_t* Jzn = a.planes + (4 * n + 3) * pw;
+    const int p = (c + y + z) & 1;
+    const int64_t rh = (int64_t)r * half;
+    const int64_t o = rh + h;
+    const int64_t dym = (int64_t)(y == 0 ? L - 1 : -1) * half, dyp = (int64_t)(y == L - 1 ? 1 - L : 1) * half;
+    const int64_t Lh = (int64_t)L * half;
+    const int64_t dzm = z == 0 ? (L - 1) * Lh : -Lh, dzp = z == L - 1 ? -(L - 1) * Lh : Lh;
+    // the x neighbour that is not at the same h: h - 1 for p = 0, h + 1 for p = 1
+    const int hs = p == 0 ? (h == 0 ? half - 1 : h - 1) : (h == half - 1 ? 0 : h + 1);
+    const int64_t os = rh + hs;
+    const uint32_t s = Sc[o];
+    const uint32_t na = Sn[o], ns = Sn[os];
+    const uint32_t e_xp = Jxc[o] ^ s ^ (p == 0 ? na : ns);
+    const uint32_t e_xm = (p == 0 ? Jxn[os] ^ ns : Jxn[o] ^ na) ^ s;
+    const uint32_t e_yp = Jyc[o] ^ s ^ Sn[o + dyp];
+    const uint32_t e_ym = Jyn[o + dym] ^ s ^ Sn[o + dym];
+    const uint32_t e_zp = Jzc[o] ^ s ^ Sn[o + dzp];
+    const uint32_t e_zm = Jzn[o + dzm] ^ s ^ Sn[o + dzm];
+    uint32_t u0, u1, u2;
+    Logic<uint32_t>::count6(e_xp, e_xm, e_yp, e_ym, e_zp, e_zm, u0, u1, u2);
+    const uint32_t c4 = d < a.cmp1 ? ~0u : 0u, c8 = d < a.cmp2 ? ~0u : 0u, c12 = d < a.cmp3 ? ~0u : 0u;
+    Sc[o] = s ^ Logic<uint32_t>::flip(u0, u1, u2, c4, c8, c12);
+}
+
+// Lane position inside the stream's site sequence (row-major, one draw each).
+struct SitePos {
+    int rl, h, y, z;  // row offset in the stream, site in the row, coordinates of the row
+};
+
+__device__ __forceinline__ void advance(SitePos& q, int by, int half, int L) {
+    q.h += by;
+    while (q.h >= half) {
+        q.h -= half;
+        ++q.rl;
+        if (++q.y == L) {
+            q.y = 0;
+            ++q.z;
+        }
+    }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kAmscWarps * 32) amsc_kernel(AmscArgs a, FlipArgs gen, StreamConst k,
+                                                               unsigned long long* tickets,
+                                                               unsigned long long base) {
+    extern __shared__ uint32_t smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t* B = smem + wid * (KIND == ISG_RNG_MT19937 ? mt_window(kAmscSlack) : 0);
+    const int half = a.half, L = a.L;
+    for (;;) {
+        unsigned long long v = 0;
+        if (lane == 0) v = atomicAdd(tickets, 1ull);
+        v = __shfl_sync(kFull, v, 0);
+        const int64_t t = (int64_t)(v - base);
+        if (t >= a.S) break;
+        StreamRegs st;
+        load_stream<KIND>(gen, t, B, st, k, lane);
+        const int64_t r0 = t * a.R;
+        const int64_t r1 = r0 + a.R < a.rows ? r0 + a.R : a.rows;
+        const int64_t D = (r1 - r0) * half;
+        SitePos q;
+        q.rl = lane / half;
+        q.h = lane - q.rl * half;
+        {
+            const int64_t r = r0 + q.rl;
+            q.y = (int)(r % L);
+            q.z = (int)(r / L);
+        }
+        int64_t done = 0;
+        if (KIND == ISG_RNG_MT19937) {
+            for (; done + 128 <= D; done += 128) {
+                uint32_t d[4];
+                mt_quad<kAmscSlack>(B, st.iA, d, k.mul, lane);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    amsc_site(a, (int)(r0 + q.rl), q.y, q.z, q.h, d[j]);
+                    advance(q, 32, half, L);
+                }
+            }
+        } else {
+            for (; done + 64 <= D; done += 64) {
+                const uint32_t dA = st.xA, dB = st.xB;
+                st.xA = minstd_mulmod(st.xA, k.a64);
+                st.xB = minstd_mulmod(st.xB, k.a64);
+                amsc_site(a, (int)(r0 + q.rl), q.y, q.z, q.h, dA);
+                advance(q, 32, half, L);
+                amsc_site(a, (int)(r0 + q.rl), q.y, q.z, q.h, dB);
+                advance(q, 32, half, L);
+            }
+        }
+        for (; done < D; done += 32) {
+            const int nvalid = D - done < 32 ? (int)(D - done) : 32;
+            uint32_t d;
+            if (KIND == ISG_RNG_MT19937) {
+                d = mt_single<kAmscSlack>(B, st.iA, lane, nvalid, k.mul);
+            } else {
+                d = st.xA;
+                const int src = lane + nvalid;
+                const uint32_t pa = __shfl_sync(kFull, st.xA, src & 31);
+                const uint32_t pb = __shfl_sync(kFull, st.xB, src & 31);
+                st.xA = src < 32 ? pa : pb;
+                st.xB = minstd_mulmod(st.xA, k.a32);
+            }
+            if (lane < nvalid) amsc_site(a, (int)(r0 + q.rl), q.y, q.z, q.h, d);
+            advance(q, 32, half, L);
+        }
+        if (KIND == ISG_RNG_MT19937) st.pos = (int)((st.pos + D) % kMtN);
+        store_stream<KIND>(gen, t, B, st, lane);
+    }
+}
+
+// Planes from the counter hash: bit b of the site word of sample b (Eq. 2).
+__global__ void amsc_init_kernel(uint32_t* planes, int64_t plane_words, int L, int half, AmscSeeds sd) {
+    const int64_t rows = (int64_t)L * L;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < 2 * plane_words;
+         w += (int64_t)gridDim.x * blockDim.x) {
+        const int c = w >= plane_words;
+        const int64_t o = w - c * plane_words;
+        const int64_t r = o / half;
+        const int h = (int)(o - r * half);
+        if (r >= rows) continue;
+        const int y = (int)(r % L), z = (int)(r / L);
+        const uint64_t i = (uint64_t)(2 * h + ((c + y + z) & 1)) + (uint64_t)L * y + (uint64_t)L * L * z;
+        uint32_t ws = 0, wx = 0, wy = 0, wz = 0;
+        for (int b = 0; b < 32; ++b) {
+            const uint32_t bit = 1u << b;
+            if (!(splitmix64(sd.S[b] ^ kSaltSpins, i) >> 63)) ws |= bit;
+            if (splitmix64(sd.J[b] ^ kSaltCouplings, 3 * i + 0) >> 63) wx |= bit;
+            if (splitmix64(sd.J[b] ^ kSaltCouplings, 3 * i + 1) >> 63) wy |= bit;
+            if (splitmix64(sd.J[b] ^ kSaltCouplings, 3 * i + 2) >> 63) wz |= bit;
+        }
+        planes[(4 * c + 0) * plane_words + o] = ws;
+        planes[(4 * c + 1) * plane_words + o] = wx;
+        planes[(4 * c + 2) * plane_words + o] = wy;
+        planes[(4 * c + 3) * plane_words + o] = wz;
+    }
+}
+
+// Per-sample count of unsatisfied bonds: the three forward bonds of every site
+// of both colours, added bit-parallel into 16-bit vertical counters (bit b of
+// counter plane j = bit j of sample b's count), flushed per thread.
+__global__ void amsc_unsat_kernel(const uint32_t* planes, int64_t plane_words, int L, int half,
+                                  unsigned long long* counts) {
+    __shared__ unsigned long long sc[32];
+    if (threadIdx.x < 32) sc[threadIdx.x] = 0;
+    __syncthreads();
+    uint32_t cnt[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) cnt[j] = 0;
+    const int64_t rows = (int64_t)L * L;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < 2 * plane_words;
+         w += (int64_t)gridDim.x * blockDim.x) {
+        const int c = w >= plane_words;
+        const int64_t o = w - c * plane_words;
+        const int64_t r = o / half;
+        const int h = (int)(o - r * half);
+        if (r >= rows) continue;
+        const int y = (int)(r % L), z = (int)(r / L);
+        const int p = (c + y + z) & 1, n = c ^ 1;
+        const uint32_t* Sn = planes + (4 * n) * plane_words;
+        const uint32_t s = planes[(4 * c) * plane_words + o];
+        const int hx = p == 0 ? h : (h == half - 1 ? 0 : h + 1);   // site x + 1 in the other colour
+        const int64_t oyp = ((int64_t)(y == L - 1 ? 0 : y + 1) + (int64_t)L * z) * half + h;
+        const int64_t ozp = ((int64_t)y + (int64_t)L * (z == L - 1 ? 0 : z + 1)) * half + h;
+        const uint32_t e[3] = {planes[(4 * c + 1) * plane_words + o] ^ s ^ Sn[r * half + hx],
+                               planes[(4 * c + 2) * plane_words + o] ^ s ^ Sn[oyp],
+                               planes[(4 * c + 3) * plane_words + o] ^ s ^ Sn[ozp]};
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            uint32_t carry = e[m];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const uint32_t tj = cnt[j] & carry;
+                cnt[j] ^= carry;
+                carry = tj;
+            }
+        }
+    }
+    for (int b = 0; b < 32; ++b) {
+        unsigned v = 0;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v |= ((cnt[j] >> b) & 1u) << j;
+        if (v) atomicAdd(&sc[b], (unsigned long long)v);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32 && sc[threadIdx.x]) atomicAdd(&counts[threadIdx.x], sc[threadIdx.x]);
+}
+
+__global__ void amsc_unpack_kernel(const uint32_t* planes, int64_t plane_words, int L, int half, int b, int8_t* out) {
+    const int64_t N = (int64_t)L * L * L;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % L), y = (int)((i / L) % L), z = (int)(i / ((int64_t)L * L));
+        const int c = (x + y + z) & 1;
+        const uint32_t w = planes[(4 * c) * plane_words + ((int64_t)y + (int64_t)L * z) * half + (x >> 1)];
+        out[i] = ((w >> b) & 1u) ? 1 : -1;
+    }
+}
+
+static unsigned amsc_grid(int64_t n, int threads, int64_t per_thread) {
+    int64_t b = (n + threads - 1) / threads;
+    const int64_t need = (n + threads * per_thread - 1) / (threads * per_thread);
+    if (b > 152 * 16) b = 152 * 16;
+    if (b < need) b = need;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+}  // namespace isg
+
+using namespace isg;
+
+extern "C" {
+
+int isg_amsc_create(int L, const uint64_t* seed_J, const uint64_t* seed_spin, uint64_t seed_rng, double beta,
+                    int rng_kind, isg_amsc** out) {
+    if (!out || !seed_J || !seed_spin) { set_error("isg_amsc_create: NULL argument"); return ISG_ERR_ARG; }
+    *out = nullptr;
+    if (L < 4 || L > 1024 || (L & 1)) { set_error("isg_amsc_create: L=%d must be even and in [4, 1024]", L); return ISG_ERR_ARG; }
+    if (!(beta > 0.0)) { set_error("isg_amsc_create: beta must be > 0 (got %g)", beta); return ISG_ERR_ARG; }
+    if (rng_kind != ISG_RNG_MINSTD && rng_kind != ISG_RNG_MT19937) {
+        set_error("isg_amsc_create: unknown rng_kind %d", rng_kind);
+        return ISG_ERR_ARG;
+    }
+    isg_amsc* m = new (std::nothrow) isg_amsc();
+    if (!m) { set_error("isg_amsc_create: out of host memory"); return ISG_ERR_NOMEM; }
+    m->L = L;
+    m->half = L / 2;
+    m->kind = rng_kind;
+    m->beta = beta;
+    thresholds(beta, m->thr);
+    m->seed_rng = seed_rng;
+    for (int b = 0; b < 32; ++b) {
+        m->seed_J[b] = seed_J[b];
+        m->seed_spin[b] = seed_spin[b];
+    }
+    m->rows = (int64_t)L * L;
+    {
+        int64_t s0 = (int64_t)L * L * L / 32768;
+        s0 = s0 < 1 ? 1 : (s0 > 8192 ? 8192 : s0);
+        m->R = (m->rows + s0 - 1) / s0;
+        m->S = (m->rows + m->R - 1) / m->R;
+    }
+    m->plane_words = (m->rows * m->half + 63) / 64 * 64;
+    const size_t rng_words = rng_kind == ISG_RNG_MT19937 ? (size_t)m->S * kMtN : (size_t)m->S;
+    cudaError_t e = cudaMalloc(&m->planes, (size_t)m->plane_words * 8 * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&m->rng, rng_words * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&m->rng_pos, (size_t)m->S * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&m->ctr, 33 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(m->ctr, 0, 33 * sizeof(unsigned long long));
+    if (e == cudaSuccess) {
+        AmscSeeds sd;
+        for (int b = 0; b < 32; ++b) {
+            sd.J[b] = seed_J[b];
+            sd.S[b] = seed_spin[b];
+        }
+        amsc_init_kernel<<<amsc_grid(2 * m->plane_words, 256, 1), 256>>>(m->planes, m->plane_words, L, m->half, sd);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        isg_sim g;  // the fields the stream-seeding kernel reads
+        g.kind = rng_kind;
+        g.seed_rng = seed_rng;
+        g.S = m->S;
+        g.rng = m->rng;
+        g.rng_pos = m->rng_pos;
+        e = launch_init_rng(&g, 0);
+        g.rng = nullptr;
+        g.rng_pos = nullptr;
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        isg_amsc_destroy(m);
+        return cuda_fail(e, "isg_amsc_create");
+    }
+    *out = m;
+    return ISG_OK;
+}
+
+void isg_amsc_destroy(isg_amsc* m) {
+    if (!m) return;
+    cudaDeviceSynchronize();
+    cudaFree(m->planes);
+    cudaFree(m->rng);
+    cudaFree(m->rng_pos);
+    cudaFree(m->ctr);
+    delete m;
+}
+
+int isg_amsc_sweep(isg_amsc* m, int64_t n, void* cuda_stream) {
+    if (!m || n < 0) { set_error("isg_amsc_sweep: bad argument"); return ISG_ERR_ARG; }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const StreamConst k = stream_const();
+    FlipArgs gen;
+    memset(&gen, 0, sizeof gen);
+    gen.rng = m->rng;
+    gen.rng_pos = m->rng_pos;
+    gen.mt = minstd_table();
+    AmscArgs a;
+    a.planes = m->planes;
+    a.plane_words = m->plane_words;
+    a.L = m->L;
+    a.half = m->half;
+    a.R = m->R;
+    a.S = m->S;
+    a.rows = m->rows;
+    if (m->kind == ISG_RNG_MT19937) {
+        a.cmp1 = m->thr[1];
+        a.cmp2 = m->thr[2];
+        a.cmp3 = m->thr[3];
+    } else {
+        a.cmp1 = (uint32_t)(((uint64_t)m->thr[1] + 1) / 2);
+        a.cmp2 = (uint32_t)(((uint64_t)m->thr[2] + 1) / 2);
+        a.cmp3 = (uint32_t)(((uint64_t)m->thr[3] + 1) / 2);
+    }
+    const size_t smem = m->kind == ISG_RNG_MT19937 ? (size_t)kAmscWarps * mt_window(kAmscSlack) * 4 : 0;
+    static int occ[2] = {0, 0};
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (!occ[m->kind]) {
+        if (m->kind == ISG_RNG_MT19937)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], amsc_kernel<ISG_RNG_MT19937>, kAmscWarps * 32, smem);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], amsc_kernel<ISG_RNG_MINSTD>, kAmscWarps * 32, smem);
+        if (occ[m->kind] < 1) occ[m->kind] = 1;
+    }
+    int64_t blocks = (int64_t)sms * occ[m->kind];
+    const int64_t need = (m->S + kAmscWarps - 1) / kAmscWarps;
+    if (blocks > need) blocks = need;
+    for (int64_t sw = 0; sw < n; ++sw) {
+        for (int c = 0; c < 2; ++c) {
+            a.c = c;
+            if (m->kind == ISG_RNG_MT19937)
+                amsc_kernel<ISG_RNG_MT19937><<<(unsigned)blocks, kAmscWarps * 32, smem, s>>>(a, gen, k, m->ctr, m->tickets);
+            else
+                amsc_kernel<ISG_RNG_MINSTD><<<(unsigned)blocks, kAmscWarps * 32, smem, s>>>(a, gen, k, m->ctr, m->tickets);
+            const cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_fail(e, "isg_amsc_sweep");
+            m->tickets += (unsigned long long)m->S + (unsigned long long)blocks * kAmscWarps;
+        }
+    }
+    m->sweeps += n;
+    return ISG_OK;
+}
+
+int isg_amsc_energies(isg_amsc* m, int64_t* E, void* cuda_stream) {
+    if (!m || !E) { set_error("isg_amsc_energies: NULL argument"); return ISG_ERR_ARG; }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    unsigned long long* counts = m->ctr + 1;
+    unsigned long long h[32];
+    cudaError_t e = cudaMemsetAsync(counts, 0, 32 * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) {
+        // at most 20000 site words per thread keeps the 16-bit counters exact (3 bonds each)
+        amsc_unsat_kernel<<<amsc_grid(2 * m->plane_words, 256, 20000), 256, 0, s>>>(m->planes, m->plane_words, m->L,
+                                                                                   m->half, counts);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, counts, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "isg_amsc_energies");
+    const int64_t threeN = 3 * (int64_t)m->L * m->L * m->L;
+    for (int b = 0; b < 32; ++b) E[b] = 2 * (int64_t)h[b] - threeN;
+    return ISG_OK;
+}
+
+int isg_amsc_read_spins(const isg_amsc* m, int sample, int8_t* out, size_t n, void* cuda_stream) {
+    const int64_t N = m ? (int64_t)m->L * m->L * m->L : 0;
+    if (!m || !out || sample < 0 || sample >= 32 || (int64_t)n < N) {
+        set_error("isg_amsc_read_spins: bad argument");
+        return ISG_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int8_t* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, (size_t)N);
+    if (e == cudaSuccess) {
+        amsc_unpack_kernel<<<amsc_grid(N, 256, 1), 256, 0, s>>>(m->planes, m->plane_words, m->L, m->half, sample, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, (size_t)N, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+    return e == cudaSuccess ? ISG_OK : cuda_fail(e, "isg_amsc_read_spins");
+}
+
+}  // extern "C"

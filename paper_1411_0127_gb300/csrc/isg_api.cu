@@ -42,7 +42,7 @@ void dev_free(isg_sim* h, void* p) {
 }
 
 // floor(2^32 exp(-4 k beta)), k = 1..3 (Sec. 4, Rmax exp(-beta dE)).
-static void thresholds(double beta, uint32_t thr[4]) {
+void thresholds(double beta, uint32_t thr[4]) {
     thr[0] = 0;
     for (int k = 1; k <= 3; ++k) {
         const double v = std::floor(4294967296.0 * std::exp(-4.0 * k * beta));

@@ -221,6 +221,8 @@ int create_sim(int L, uint64_t seed_J, uint64_t seed_spin, uint64_t seed_rng, do
                isg_sim** out);
 void destroy_sim(isg_sim* h);
 size_t sim_device_bytes(int L, int rng_kind, bool force32);
+// floor(2^32 exp(-4 k beta)) for k = 1..3, thr[0] = 0 (Sec. 4)
+void thresholds(double beta, uint32_t thr[4]);
 
 // kernels (launchers) implemented in the .cu files
 cudaError_t launch_init_planes(isg_sim* h, cudaStream_t s);

@@ -59,6 +59,12 @@ def batch_samples(n: int = 512, sampler_seed: int = 7) -> list[BatchSample]:
     return [BatchSample(int(Ls[s]), 1000 + s, (2 * s, 2 * s + 1), float(Ts[s])) for s in range(n)]
 
 
+def amsc_seeds(L: int) -> tuple[list[int], list[int]]:
+    """Seeds of the 32 systems of an asynchronous multispin ensemble of size L:
+    system b has seed_J = 5000 + 64 b + L and seed_spin = 5001 + 64 b + L."""
+    return ([5000 + 64 * b + L for b in range(32)], [5001 + 64 * b + L for b in range(32)])
+
+
 @dataclass(frozen=True)
 class Job:
     arrival: float        # seconds from the start of the trace

@@ -48,6 +48,23 @@ def test_create_rejects_bad_arguments_without_touching_the_device(isg):
     assert lib.isg_create(8, 1, 2, 1.0, 0, None) == isg.ISG_ERR_ARG
 
 
+def test_amsc_create_rejects_bad_arguments_without_touching_the_device(isg):
+    h = ctypes.c_void_p()
+    lib = isg.lib()
+    seeds = (ctypes.c_uint64 * 32)(*range(32))
+    for L, beta, kind in [(5, 1.0, 0), (2, 1.0, 0), (1026, 1.0, 0), (8, 0.0, 0), (8, -1.0, 1),
+                          (8, float("nan"), 0), (8, 1.0, 2)]:
+        assert lib.isg_amsc_create(L, seeds, seeds, 3, beta, kind, ctypes.byref(h)) == isg.ISG_ERR_ARG
+        assert h.value is None
+    assert lib.isg_amsc_create(8, None, seeds, 3, 1.0, 0, ctypes.byref(h)) == isg.ISG_ERR_ARG
+    assert lib.isg_amsc_create(8, seeds, seeds, 3, 1.0, 0, None) == isg.ISG_ERR_ARG
+    assert lib.isg_amsc_sweep(None, 1, None) == isg.ISG_ERR_ARG
+    assert lib.isg_amsc_energies(None, None, None) == isg.ISG_ERR_ARG
+    assert lib.isg_amsc_read_spins(None, 0, None, 0, None) == isg.ISG_ERR_ARG
+    with pytest.raises(ValueError):
+        isg.Amsc(8, [1] * 31, [2] * 32, 3, 1.0, "minstd")
+
+
 def test_other_host_side_checks(isg):
     lib = isg.lib()
     assert lib.isg_info(None, None, None, None, None, None) == isg.ISG_ERR_ARG
