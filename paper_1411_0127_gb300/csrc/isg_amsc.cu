@@ -51,51 +51,38 @@ struct AmscSeeds {
     uint64_t J[32], S[32];
 };
 
-// One site word of colour c at row r = y + L z, position h.
-__device__ __forceinline__ void amsc_site(const AmscArgs& a, int r, int y, int z, int h, uint32_t d) {
-    const int L = a.L, half = a.half, c = a.c, n = c ^ 1;
+// The planes of one colour pass: the updated colour's spins (read and written,
+// each word by one lane only) and the seven read-only planes.
+struct AmscPtrs {
+    uint32_t* Sc;
+    const uint32_t *Jxc, *Jyc, *Jzc, *Sn, *Jxn, *Jyn, *Jzn;
+};
+
+__device__ __forceinline__ AmscPtrs amsc_ptrs(const AmscArgs& a) {
+    const int c = a.c, n = c ^ 1;
     const int64_t pw = a.plane_words;
-    uint32_t* Sc = a.planes + (4 * c) * pw;
-    const uint32_t* Jxc = a.planes + (4 * c + 1) * pw;
-    const uint32_t* Jyc = a.planes + (4 * c + 2) * pw;
-    const uint32_t* Jzc = a.planes + (4 * c + 3) * pw;
-    const uint32_t* Sn = a.planes + (4 * n) * pw;
-    const uint32_t* Jxn = a.planes + (4 * n + 1) * pw;
-    const uint32_t* Jyn = a.planes + (4 * n + 2) * pw;
-    const uint32_t* Jzn = a.planes + (4 * n + 3) * pw;
-    const int p = (c + y + z) & 1;
-    const int64_t rh = (int64_t)r * half;
-    const int64_t o = rh + h;
-    const int64_t dym = (int64_t)(y == 0 ? L - 1 : -1) * half, dyp = (int64_t)(y == L - 1 ? 1 - L : 1) * half;
-    const int64_t Lh = (int64_t)L * half;
-    const int64_t dzm = z == 0 ? (L - 1) * Lh : -Lh, dzp = z == L - 1 ? -(L - 1) * Lh : Lh;
-    // the x neighbour that is not at the same h: h - 1 for p = 0, h + 1 for p = 1
-    const int hs = p == 0 ? (h == 0 ? half - 1 : h - 1) : (h == half - 1 ? 0 : h + 1);
-    const int64_t os = rh + hs;
-    const uint32_t s = Sc[o];
-    const uint32_t na = Sn[o], ns = Sn[os];
-    const uint32_t e_xp = Jxc[o] ^ s ^ (p == 0 ? na : ns);
-    const uint32_t e_xm = (p == 0 ? Jxn[os] ^ ns : Jxn[o] ^ na) ^ s;
-    const uint32_t e_yp = Jyc[o] ^ s ^ Sn[o + dyp];
-    const uint32_t e_ym = Jyn[o + dym] ^ s ^ Sn[o + dym];
-    const uint32_t e_zp = Jzc[o] ^ s ^ Sn[o + dzp];
-    const uint32_t e_zm = Jzn[o + dzm] ^ s ^ Sn[o + dzm];
-    uint32_t u0, u1, u2;
-    Logic<uint32_t>::count6(e_xp, e_xm, e_yp, e_ym, e_zp, e_zm, u0, u1, u2);
-    const uint32_t c4 = d < a.cmp1 ? ~0u : 0u, c8 = d < a.cmp2 ? ~0u : 0u, c12 = d < a.cmp3 ? ~0u : 0u;
-    Sc[o] = s ^ Logic<uint32_t>::flip(u0, u1, u2, c4, c8, c12);
+    AmscPtrs P;
+    P.Sc = a.planes + (4 * c) * pw;
+    P.Jxc = a.planes + (4 * c + 1) * pw;
+    P.Jyc = a.planes + (4 * c + 2) * pw;
+    P.Jzc = a.planes + (4 * c + 3) * pw;
+    P.Sn = a.planes + (4 * n) * pw;
+    P.Jxn = a.planes + (4 * n + 1) * pw;
+    P.Jyn = a.planes + (4 * n + 2) * pw;
+    P.Jzn = a.planes + (4 * n + 3) * pw;
+    return P;
 }
 
 // Lane position inside the stream's site sequence (row-major, one draw each).
 struct SitePos {
-    int rl, h, y, z;  // row offset in the stream, site in the row, coordinates of the row
+    int r, h, y, z;  // row r = y + L z of the site, its position in the row
 };
 
 __device__ __forceinline__ void advance(SitePos& q, int by, int half, int L) {
     q.h += by;
     while (q.h >= half) {
         q.h -= half;
-        ++q.rl;
+        ++q.r;
         if (++q.y == L) {
             q.y = 0;
             ++q.z;
@@ -103,6 +90,57 @@ __device__ __forceinline__ void advance(SitePos& q, int by, int half, int L) {
     }
 }
 
+// The words one site update reads: its spin word and forward couplings, and
+// for each of the six bonds the neighbour's spin word (backward couplings from
+// the other colour's planes at the -x, -y, -z neighbour).  Offsets fit in 32
+// bits (a plane has at most 1024^2 * 512 words).
+struct SiteIn {
+    int o;
+    uint32_t s, jxp, jyp, jzp, sxp, sxm, jxm, syp, sym, jym, szp, szm, jzm;
+};
+
+__device__ __forceinline__ void site_load(const AmscPtrs& P, int L, int half, int c, const SitePos& q, SiteIn& w) {
+    const int p = (c + q.y + q.z) & 1;
+    const int rh = q.r * half;
+    const int o = rh + q.h;
+    const int dym = (q.y == 0 ? L - 1 : -1) * half, dyp = (q.y == L - 1 ? 1 - L : 1) * half;
+    const int Lh = L * half;
+    const int dzm = q.z == 0 ? (L - 1) * Lh : -Lh, dzp = q.z == L - 1 ? -(L - 1) * Lh : Lh;
+    // the x neighbour that is not at the same h: h - 1 for p = 0, h + 1 for p = 1
+    const int hs = p == 0 ? (q.h == 0 ? half - 1 : q.h - 1) : (q.h == half - 1 ? 0 : q.h + 1);
+    const int os = rh + hs;
+    w.o = o;
+    w.s = P.Sc[o];
+    w.jxp = __ldg(P.Jxc + o);
+    w.jyp = __ldg(P.Jyc + o);
+    w.jzp = __ldg(P.Jzc + o);
+    const uint32_t na = __ldg(P.Sn + o), ns = __ldg(P.Sn + os);
+    w.sxp = p == 0 ? na : ns;
+    w.sxm = p == 0 ? ns : na;
+    w.jxm = __ldg(P.Jxn + (p == 0 ? os : o));
+    w.syp = __ldg(P.Sn + o + dyp);
+    w.sym = __ldg(P.Sn + o + dym);
+    w.jym = __ldg(P.Jyn + o + dym);
+    w.szp = __ldg(P.Sn + o + dzp);
+    w.szm = __ldg(P.Sn + o + dzm);
+    w.jzm = __ldg(P.Jzn + o + dzm);
+}
+
+// Sec. 4: e = J ^ s ^ s' per bond, u = sum of the six e (bit-sliced), and the
+// draw's comparisons broadcast to all 32 systems as all-ones / all-zeros masks.
+__device__ __forceinline__ void site_flip(uint32_t* Sc, const SiteIn& w, uint32_t d, const AmscArgs& a) {
+    const uint32_t s = w.s;
+    uint32_t u0, u1, u2;
+    Logic<uint32_t>::count6(w.jxp ^ s ^ w.sxp, w.jxm ^ s ^ w.sxm, w.jyp ^ s ^ w.syp, w.jym ^ s ^ w.sym,
+                            w.jzp ^ s ^ w.szp, w.jzm ^ s ^ w.szm, u0, u1, u2);
+    const uint32_t c4 = d < a.cmp1 ? ~0u : 0u, c8 = d < a.cmp2 ? ~0u : 0u, c12 = d < a.cmp3 ? ~0u : 0u;
+    Sc[w.o] = s ^ Logic<uint32_t>::flip(u0, u1, u2, c4, c8, c12);
+}
+
+// One warp per stream; lane l updates the sites l, l + 32, ... of the stream's
+// sequence with the draws of the same index.  Four blocks of 32 sites at a time:
+// the four sites' loads are issued before the draws are made and the flips
+// applied, so each lane has 52 independent loads in flight.
 template <int KIND>
 __global__ void __launch_bounds__(kAmscWarps * 32) amsc_kernel(AmscArgs a, FlipArgs gen, StreamConst k,
                                                                unsigned long long* tickets,
@@ -110,7 +148,8 @@ __global__ void __launch_bounds__(kAmscWarps * 32) amsc_kernel(AmscArgs a, FlipA
     extern __shared__ uint32_t smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint32_t* B = smem + wid * (KIND == ISG_RNG_MT19937 ? mt_window(kAmscSlack) : 0);
-    const int half = a.half, L = a.L;
+    const int half = a.half, L = a.L, c = a.c;
+    const AmscPtrs P = amsc_ptrs(a);
     for (;;) {
         unsigned long long v = 0;
         if (lane == 0) v = atomicAdd(tickets, 1ull);
@@ -123,34 +162,34 @@ __global__ void __launch_bounds__(kAmscWarps * 32) amsc_kernel(AmscArgs a, FlipA
         const int64_t r1 = r0 + a.R < a.rows ? r0 + a.R : a.rows;
         const int64_t D = (r1 - r0) * half;
         SitePos q;
-        q.rl = lane / half;
-        q.h = lane - q.rl * half;
         {
-            const int64_t r = r0 + q.rl;
-            q.y = (int)(r % L);
-            q.z = (int)(r / L);
+            const int rl = lane / half;
+            q.r = (int)r0 + rl;
+            q.h = lane - rl * half;
+            q.y = q.r % L;
+            q.z = q.r / L;
         }
         int64_t done = 0;
-        if (KIND == ISG_RNG_MT19937) {
-            for (; done + 128 <= D; done += 128) {
-                uint32_t d[4];
-                mt_quad<kAmscSlack>(B, st.iA, d, k.mul, lane);
+        for (; done + 128 <= D; done += 128) {
+            SiteIn w[4];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    amsc_site(a, (int)(r0 + q.rl), q.y, q.z, q.h, d[j]);
-                    advance(q, 32, half, L);
-                }
-            }
-        } else {
-            for (; done + 64 <= D; done += 64) {
-                const uint32_t dA = st.xA, dB = st.xB;
-                st.xA = minstd_mulmod(st.xA, k.a64);
-                st.xB = minstd_mulmod(st.xB, k.a64);
-                amsc_site(a, (int)(r0 + q.rl), q.y, q.z, q.h, dA);
-                advance(q, 32, half, L);
-                amsc_site(a, (int)(r0 + q.rl), q.y, q.z, q.h, dB);
+            for (int j = 0; j < 4; ++j) {
+                site_load(P, L, half, c, q, w[j]);
                 advance(q, 32, half, L);
             }
+            uint32_t d[4];
+            if (KIND == ISG_RNG_MT19937) {
+                mt_quad<kAmscSlack>(B, st.iA, d, k.mul, lane);
+            } else {
+                d[0] = st.xA;
+                d[1] = st.xB;
+                d[2] = minstd_mulmod(st.xA, k.a64);
+                d[3] = minstd_mulmod(st.xB, k.a64);
+                st.xA = minstd_mulmod(d[2], k.a64);
+                st.xB = minstd_mulmod(d[3], k.a64);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) site_flip(P.Sc, w[j], d[j], a);
         }
         for (; done < D; done += 32) {
             const int nvalid = D - done < 32 ? (int)(D - done) : 32;
@@ -165,7 +204,11 @@ __global__ void __launch_bounds__(kAmscWarps * 32) amsc_kernel(AmscArgs a, FlipA
                 st.xA = src < 32 ? pa : pb;
                 st.xB = minstd_mulmod(st.xA, k.a32);
             }
-            if (lane < nvalid) amsc_site(a, (int)(r0 + q.rl), q.y, q.z, q.h, d);
+            if (lane < nvalid) {
+                SiteIn w;
+                site_load(P, L, half, c, q, w);
+                site_flip(P.Sc, w, d, a);
+            }
             advance(q, 32, half, L);
         }
         if (KIND == ISG_RNG_MT19937) st.pos = (int)((st.pos + D) % kMtN);
