@@ -7,7 +7,7 @@ code with the CUDA library in ``paper_1411_0127_gb300``.
 
 Passages followed (arXiv:1411.0127): Eq. (1) Hamiltonian, Eq. (2) bimodal
 couplings, Sec. 1 checkerboard colours, Sec. 4 Metropolis rule and integer
-threshold comparison, Sec. 3 MINSTD and MT19937.
+threshold comparison, Sec. 3 MINSTD, MT19937 and Parisi-Rapuano.
 """
 from __future__ import annotations
 
@@ -23,6 +23,7 @@ _LIB = os.path.join(_HERE, "libisg_oracle.so")
 
 RNG_MINSTD = 0
 RNG_MT19937 = 1
+RNG_PR = 2
 
 
 def build(force: bool = False) -> str:
@@ -63,6 +64,7 @@ def lib() -> ctypes.CDLL:
             "or_num_streams": (i64, [i32]),
             "or_mt19937_outputs": (None, [u32, vp, i64]),
             "or_minstd_outputs": (None, [u32, vp, i64]),
+            "or_pr_outputs": (None, [u64, vp, i64]),
             "or_unsatisfied": (i32, [ctypes.c_int8, vp, vp]),
             "or_accept": (i32, [i32, u32, vp]),
             "or_create": (vp, [i32, u64, u64, dbl, i32]),
@@ -123,6 +125,13 @@ def mt19937_outputs(seed: int, n: int) -> np.ndarray:
 def minstd_outputs(x0: int, n: int) -> np.ndarray:
     out = np.empty(n, dtype=np.uint32)
     lib().or_minstd_outputs(x0, _ptr(out), n)
+    return out
+
+
+def pr_outputs(v: int, n: int) -> np.ndarray:
+    """Parisi-Rapuano outputs from seed word v (see or_pr_outputs)."""
+    out = np.empty(n, dtype=np.uint32)
+    lib().or_pr_outputs(v & (2**64 - 1), _ptr(out), n)
     return out
 
 

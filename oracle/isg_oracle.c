@@ -120,13 +120,52 @@ void or_minstd_outputs(uint32_t x0, uint32_t *out, int64_t n)
     for (int64_t k = 0; k < n; ++k) out[k] = minstd_next(&x);
 }
 
-/* One stream: the 32-bit draw d compared with the thresholds.  MT19937 gives
- * its tempered output; MINSTD's state (at most 2^31 - 2) is doubled so that
- * both kinds are compared with the same 32-bit table. */
+/* Parisi-Rapuano (Sec. 3): ira[i] = ira[i-24] + ira[i-55] (mod 2^32) and the
+ * output is R = ira[i] ^ ira[i-61].  The state is the 61 most recent words,
+ * kept as a ring: w[k] is ira[i-61] for the next i, so ira[i-m] sits at
+ * w[(k + 61 - m) % 61].  Seeding (the paper gives none): ira[j] = the upper
+ * 32 bits of SplitMix64(v, j) for j = 0..60, with ira[60] made odd so that the
+ * low bits (a lag-(24, 55) shift register) never start from all zeros; the
+ * first output is R for i = 61. */
+typedef struct {
+    uint32_t w[61];
+    int k;
+} pr_state;
+
+static void pr_seed(pr_state *p, uint64_t v)
+{
+    for (int j = 0; j < 61; ++j) p->w[j] = (uint32_t)(or_splitmix64(v, (uint64_t)j) >> 32);
+    p->w[60] |= 1u;
+    p->k = 0;
+}
+
+static uint32_t pr_next(pr_state *p)
+{
+    int k = p->k;
+    uint32_t lag24 = p->w[(k + 61 - 24) % 61];
+    uint32_t lag55 = p->w[(k + 61 - 55) % 61];
+    uint32_t lag61 = p->w[k];
+    uint32_t v = lag24 + lag55;
+    p->w[k] = v; /* ira[i] replaces ira[i-61] */
+    p->k = (k + 1) % 61;
+    return v ^ lag61;
+}
+
+void or_pr_outputs(uint64_t v, uint32_t *out, int64_t n)
+{
+    pr_state p;
+    pr_seed(&p, v);
+    for (int64_t k = 0; k < n; ++k) out[k] = pr_next(&p);
+}
+
+/* One stream: the 32-bit draw d compared with the thresholds.  MT19937 and
+ * Parisi-Rapuano give their 32-bit outputs; MINSTD's state (at most 2^31 - 2)
+ * is doubled so that every kind is compared with the same 32-bit table. */
 typedef struct {
     int kind;
     uint32_t minstd;
     mt_state mt;
+    pr_state pr;
     int64_t used; /* draws consumed so far */
 } stream_t;
 
@@ -134,7 +173,18 @@ static uint32_t stream_draw(stream_t *st)
 {
     st->used++;
     if (st->kind == OR_RNG_MT19937) return mt_next(&st->mt);
+    if (st->kind == OR_RNG_PR) return pr_next(&st->pr);
     return minstd_next(&st->minstd) << 1;
+}
+
+/* Stream t of a lattice from v_t = SplitMix64(seed_rng ^ K_R, t). */
+static void stream_seed(stream_t *st, int kind, uint64_t v)
+{
+    memset(st, 0, sizeof *st);
+    st->kind = kind;
+    if (kind == OR_RNG_MT19937) mt_seed(&st->mt, (uint32_t)v);
+    else if (kind == OR_RNG_PR) pr_seed(&st->pr, v);
+    else st->minstd = 1u + (uint32_t)(v % 2147483646u);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -185,7 +235,7 @@ or_sim *or_create2(int L, uint64_t seed_J, uint64_t seed_spin, uint64_t seed_rng
 {
     if (L < 4 || (L & 1) || L > 2048) return NULL;
     if (!(beta > 0.0)) return NULL; /* rejects 0, negatives and NaN; +inf allowed */
-    if (kind != OR_RNG_MINSTD && kind != OR_RNG_MT19937) return NULL;
+    if (kind != OR_RNG_MINSTD && kind != OR_RNG_MT19937 && kind != OR_RNG_PR) return NULL;
     or_sim *o = (or_sim *)calloc(1, sizeof(or_sim));
     if (!o) return NULL;
     o->L = L;
@@ -207,12 +257,8 @@ or_sim *or_create2(int L, uint64_t seed_J, uint64_t seed_spin, uint64_t seed_rng
                 (or_splitmix64(seed_J ^ SALT_COUPLINGS, 3 * (uint64_t)i + (uint64_t)d) >> 63) ? -1 : 1;
         o->s[i] = (or_splitmix64(seed_spin ^ SALT_SPINS, (uint64_t)i) >> 63) ? -1 : 1;
     }
-    for (int64_t t = 0; t < o->S; ++t) {
-        uint64_t v = or_splitmix64(seed_rng ^ SALT_STREAMS, (uint64_t)t);
-        o->st[t].kind = kind;
-        if (kind == OR_RNG_MT19937) mt_seed(&o->st[t].mt, (uint32_t)v);
-        else o->st[t].minstd = 1u + (uint32_t)(v % 2147483646u);
-    }
+    for (int64_t t = 0; t < o->S; ++t)
+        stream_seed(&o->st[t], kind, or_splitmix64(seed_rng ^ SALT_STREAMS, (uint64_t)t));
     o->E0 = or_energy(o);
     o->dE = 0;
     return o;
@@ -429,6 +475,7 @@ void or_acceptance_trial(int kind, uint32_t seed, double beta, int64_t n, int64_
     memset(&st, 0, sizeof st);
     st.kind = kind;
     if (kind == OR_RNG_MT19937) mt_seed(&st.mt, seed);
+    else if (kind == OR_RNG_PR) pr_seed(&st.pr, seed);
     else st.minstd = seed;
     or_thresholds(beta, thr);
     for (int u = 0; u < 3; ++u) {

@@ -27,7 +27,7 @@
 extern "C" {
 #endif
 
-enum { OR_RNG_MINSTD = 0, OR_RNG_MT19937 = 1 };
+enum { OR_RNG_MINSTD = 0, OR_RNG_MT19937 = 1, OR_RNG_PR = 2 };
 
 typedef struct or_sim or_sim;
 
@@ -46,6 +46,9 @@ int64_t or_num_streams(int L);
 /* Raw generator streams (for the generator pins). */
 void or_mt19937_outputs(uint32_t seed, uint32_t *out, int64_t n);   /* init_genrand(seed) */
 void or_minstd_outputs(uint32_t x0, uint32_t *out, int64_t n);      /* successive states */
+/* Parisi-Rapuano (Sec. 3) from the seed word v: ira[j] = SplitMix64(v, j) >> 32
+ * for j < 61, ira[60] |= 1; output n is ira[61+n] ^ ira[n]. */
+void or_pr_outputs(uint64_t v, uint32_t *out, int64_t n);
 
 /* Number of unsatisfied bonds around a site (0..6); s, nb[k], J[k] are +-1. */
 int or_unsatisfied(int8_t s, const int8_t nb[6], const int8_t J[6]);
@@ -82,7 +85,8 @@ void    or_move_counts(const or_sim *s, int64_t attempts[7], int64_t accepts[7])
 /* The next n draws of stream t, without advancing it. */
 void    or_peek_draws(const or_sim *s, int64_t t, int64_t n, uint32_t *out);
 /* n Metropolis decisions for each u = 0,1,2 with draws from one stream of the
- * given kind and seed word (MT19937: init_genrand(seed); MINSTD: x0 = seed). */
+ * given kind and seed word (MT19937: init_genrand(seed); MINSTD: x0 = seed;
+ * Parisi-Rapuano: seed word v = seed). */
 void    or_acceptance_trial(int kind, uint32_t seed, double beta, int64_t n, int64_t accepts[3]);
 
 #ifdef __cplusplus

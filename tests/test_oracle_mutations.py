@@ -40,6 +40,11 @@ MUTANTS = {
     "hash keys": ("if (o->s[i] == 1) h ^= or_splitmix64(SALT_HASH, (uint64_t)i);",
                   "if (o->s[i] == 1) h ^= or_splitmix64(SALT_HASH, (uint64_t)i + 1);"),
     "stream rows": ("if (s > 8192) s = 8192;", "if (s > 4096) s = 4096;"),
+    "Parisi-Rapuano short lag": ("p->w[(k + 61 - 24) % 61]", "p->w[(k + 61 - 23) % 61]"),
+    "Parisi-Rapuano output lag": ("uint32_t lag61 = p->w[k];", "uint32_t lag61 = p->w[(k + 1) % 61];"),
+    "Parisi-Rapuano xor for add": ("uint32_t v = lag24 + lag55;", "uint32_t v = lag24 ^ lag55;"),
+    "Parisi-Rapuano seeding": ("p->w[j] = (uint32_t)(or_splitmix64(v, (uint64_t)j) >> 32);",
+                               "p->w[j] = (uint32_t)or_splitmix64(v, (uint64_t)j);"),
 }
 
 # pins that need no tmp_path fixture, with their parameters
@@ -60,6 +65,8 @@ PIN_CALLS = [
     (pins.test_overlap_and_hash_properties, {}),
     (pins.test_stream_partition_and_draw_counts, {}),
     (pins.test_coupling_and_spin_balance, {}),
+    (pins.test_parisi_rapuano_companion_matrix_powers, {"v": 77}),
+    (pins.test_parisi_rapuano_low_bits_polynomial_jump, {}),
 ]
 
 

@@ -14,10 +14,10 @@ import numpy as np
 import pytest
 
 import oracle
-from oracle import OracleSim, RNG_MINSTD, RNG_MT19937
+from oracle import OracleSim, RNG_MINSTD, RNG_MT19937, RNG_PR
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
-KINDS = [RNG_MINSTD, RNG_MT19937]
+KINDS = [RNG_MINSTD, RNG_MT19937, RNG_PR]
 
 
 # --------------------------------------------------------------------------
@@ -98,6 +98,131 @@ def _thr_mp(beta):
             assert 1e-5 < frac < 1 - 1e-5
         out.append(fl)
     return out
+
+
+# Parisi-Rapuano (Sec. 3): ira[i] = ira[i-24] + ira[i-55] mod 2^32, R = ira[i] ^ ira[i-61].
+# The seeding is this build's reading (the paper gives none): ira[j] = upper 32
+# bits of SplitMix64(v, j), j < 61, ira[60] made odd.
+
+def _pr_initial_words(v):
+    w = [oracle.splitmix64(v, j) >> 32 for j in range(61)]
+    w[60] |= 1
+    return w
+
+
+def _pr_step_matrix():
+    """61 x 61 companion matrix of the window (ira[i-61], ..., ira[i-1]) -> the
+    window one step later; its last row forms ira[i] from lags 24 and 55."""
+    M = np.zeros((61, 61), dtype=object)
+    for j in range(60):
+        M[j, j + 1] = 1
+    M[60, 61 - 24] = 1
+    M[60, 61 - 55] = 1
+    return M
+
+
+def _matvec_power(M, n, vec, mod):
+    """M^n vec (mod `mod`) by binary powering: a different computation from the
+    oracle's ring-buffer iteration."""
+    vec = np.array(vec, dtype=object)
+    P = M.copy()
+    while n:
+        if n & 1:
+            vec = P.dot(vec) % mod
+        n >>= 1
+        if n:
+            P = P.dot(P) % mod
+    return vec
+
+
+@pytest.mark.parametrize("v", [0, 77, 2**64 - 1])
+def test_parisi_rapuano_companion_matrix_powers(v):
+    """Output n = ira[61+n] ^ ira[n]: the windows after n and n + 1 steps come
+    from powers of the companion matrix mod 2^32, not from iteration."""
+    ns = [0, 1, 23, 24, 54, 55, 60, 61, 62, 500, 4099]
+    out = oracle.pr_outputs(v, max(ns) + 1)
+    s0 = _pr_initial_words(v)
+    M = _pr_step_matrix()
+    for n in ns:
+        a = _matvec_power(M, n, s0, 2**32)
+        b = M.dot(a) % 2**32
+        assert int(out[n]) == (int(b[60]) ^ int(a[0])), n
+
+
+def _gf2_mulmod(a, b, p, deg):
+    r = 0
+    while b:
+        if b & 1:
+            r ^= a
+        b >>= 1
+        a <<= 1
+        if a >> deg & 1:
+            a ^= p
+    return r
+
+
+def _gf2_xpow(n, p, deg):
+    """x^n mod p(x) over GF(2), polynomials as bit masks."""
+    r, base = 1, 2
+    while n:
+        if n & 1:
+            r = _gf2_mulmod(r, base, p, deg)
+        base = _gf2_mulmod(base, base, p, deg)
+        n >>= 1
+    return r
+
+
+def test_parisi_rapuano_low_bits_polynomial_jump():
+    """The low bits b_i of ira obey b_i = b_(i-24) ^ b_(i-55) (addition mod 2):
+    characteristic polynomial x^55 + x^31 + 1.  Far along the stream (n ~ 10^6)
+    the low bit of each output equals b_(61+n) ^ b_n computed by a GF(2)
+    polynomial jump from the initial window b_6 .. b_60."""
+    v = 2024
+    base = 10**6
+    out = oracle.pr_outputs(v, base + 40)
+    w = _pr_initial_words(v)
+    window = [w[6 + j] & 1 for j in range(55)]
+    p, deg = (1 << 55) | (1 << 31) | 1, 55
+
+    def bit(i):  # b_i for i >= 6
+        c = _gf2_xpow(i - 6, p, deg)
+        return sum(window[j] for j in range(55) if c >> j & 1) & 1
+
+    for n in range(base, base + 40):
+        assert int(out[n]) & 1 == bit(61 + n) ^ bit(n), n
+
+
+def test_parisi_rapuano_trinomial_period_structure():
+    """x^55 + x^24 + 1 (and its reciprocal) is the primitive trinomial behind
+    the lags (24, 55): x^(2^55 - 1) = 1 mod p, and x^((2^55 - 1)/q) != 1 for each
+    prime factor q of 2^55 - 1 (found here by trial division), so the low bits
+    of a seeded stream have the full period 2^55 - 1."""
+    p, deg = (1 << 55) | (1 << 31) | 1, 55
+    order = 2**55 - 1
+    assert _gf2_xpow(order, p, deg) == 1
+    n, q, factors = order, 2, set()
+    while q * q <= n:
+        while n % q == 0:
+            factors.add(q)
+            n //= q
+        q += 1
+    if n > 1:
+        factors.add(n)
+    assert len(factors) >= 2
+    for f in factors:
+        assert _gf2_xpow(order // f, p, deg) != 1, f
+
+
+def test_parisi_rapuano_uniformity():
+    """10^6 outputs: odd fraction and the top-byte histogram of a uniform
+    32-bit generator (5 sigma / chi-square with 255 degrees of freedom)."""
+    out = oracle.pr_outputs(31337, 10**6)
+    n = out.size
+    assert abs((out & 1).mean() - 0.5) < 5 * 0.5 / math.sqrt(n)
+    h = np.bincount(out >> 24, minlength=256)
+    e = n / 256
+    chi2 = ((h - e) ** 2 / e).sum()
+    assert chi2 < 255 + 5 * math.sqrt(2 * 255)
 
 
 @pytest.mark.parametrize("beta", [1 / 1.1, 1 / 0.7, 1 / 0.9, 1 / 0.5, 1 / 1.5, 0.2, 0.05, 3.0])
@@ -256,7 +381,7 @@ def test_thread_count_does_not_change_result():
 # --------------------------------------------------------------------------
 # Acceptance law: frequencies per u against min(1, exp(-beta dE)) (Sec. 4)
 
-@pytest.mark.parametrize("kind,seed", [(RNG_MT19937, 99), (RNG_MINSTD, 12345)])
+@pytest.mark.parametrize("kind,seed", [(RNG_MT19937, 99), (RNG_MINSTD, 12345), (RNG_PR, 4242)])
 def test_acceptance_frequency_1e8(kind, seed):
     beta = 1 / 1.1
     n = 10**8
@@ -347,7 +472,7 @@ def test_coupling_and_spin_balance():
 
 
 @pytest.mark.parametrize("args", [(5, 0.5, 0), (2, 0.5, 0), (8, 0.0, 0), (8, -1.0, 0),
-                                  (8, float("nan"), 0), (8, 0.5, 2), (2050, 0.5, 0)])
+                                  (8, float("nan"), 0), (8, 0.5, 3), (2050, 0.5, 0)])
 def test_invalid_arguments_rejected(args):
     L, beta, kind = args
     with pytest.raises(ValueError):
