@@ -266,7 +266,8 @@ def other_configs_section(stream) -> dict:
     out = {}
     cases = [("L32_minstd_T1.1", workloads.SMALL, 2000), ("L256_minstd_T0.7", workloads.MEDIUM_MINSTD, 1000),
              ("L256_mt19937_T0.7", workloads.MEDIUM_MT, 1000),
-             ("L1024_minstd_T0.9", dataclasses.replace(workloads.LARGE, kind="minstd"), 300)]
+             ("L1024_minstd_T0.9", dataclasses.replace(workloads.LARGE, kind="minstd"), 300),
+             ("L1024_parisi_rapuano_T0.9", dataclasses.replace(workloads.LARGE, kind="parisi_rapuano"), 300)]
     for name, w, n in cases:
         s = isg.Sim(w.L, w.seed_J, w.seed_spin, w.beta, w.kind)
         s.sweep(10, stream)
@@ -286,8 +287,8 @@ def rng_section() -> dict:
     64 x 256 threads x 2^15 numbers x 10 = 5.4e9 instances; here 8192 streams x
     2^16 numbers x 10 calls (the same total), counting odd outputs."""
     import paper_1411_0127_gb300 as isg
-    out = {"paper_gtx_titan_instances_per_s": {"mt19937": 14.1e9, "minstd": 8.9e10}}
-    for kind in ("mt19937", "minstd"):
+    out = {"paper_gtx_titan_instances_per_s": {"mt19937": 14.1e9, "minstd": 8.9e10, "parisi_rapuano": 16.8e9}}
+    for kind in ("mt19937", "minstd", "parisi_rapuano"):
         isg.rng_count_odd(kind, 1, 8192, 4096)                 # warm-up
         total_ms, odd, n = 0.0, 0, 0
         for rep in range(10):
@@ -321,7 +322,8 @@ def amsc_section(stream) -> dict:
     import paper_1411_0127_gb300 as isg
     from paper_1411_0127_gb300 import workloads
     out = {"paper_gtx_titan_psflip": {"minstd": 3.0, "mt19937": 5.0}, "bytes_per_attempt": 36 / 32}
-    for L, kind, n in [(1024, "mt19937", 40), (1024, "minstd", 40), (256, "mt19937", 400)]:
+    for L, kind, n in [(1024, "mt19937", 40), (1024, "minstd", 40), (1024, "parisi_rapuano", 40),
+                       (256, "mt19937", 400)]:
         seed_J, seed_spin = workloads.amsc_seeds(L)
         m = isg.Amsc(L, seed_J, seed_spin, 12345, 1 / 0.9, kind)
         m.sweep(3, stream)

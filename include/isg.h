@@ -47,7 +47,7 @@ enum {
     ISG_ERR_STATE = -6     /* call not valid in the handle's current state */
 };
 
-enum { ISG_RNG_MINSTD = 0, ISG_RNG_MT19937 = 1 };
+enum { ISG_RNG_MINSTD = 0, ISG_RNG_MT19937 = 1, ISG_RNG_PARISI_RAPUANO = 2 };
 
 typedef struct isg_sim isg_sim;
 typedef struct isg_batch isg_batch;
@@ -60,7 +60,10 @@ typedef struct isg_batch isg_batch;
  *   seed_spin  initial spins and the RNG streams of this replica
  *   beta       inverse temperature, > 0, may be +INFINITY; 0, negative or NaN
  *              give ISG_ERR_ARG (beta = 0 would need a threshold of 2^32)
- *   rng_kind   ISG_RNG_MINSTD (Sec. 3 Lehmer generator) or ISG_RNG_MT19937
+ *   rng_kind   ISG_RNG_MINSTD (Sec. 3 Lehmer generator), ISG_RNG_MT19937 or
+ *              ISG_RNG_PARISI_RAPUANO (Sec. 3: ira[i] = ira[i-24] + ira[i-55],
+ *              draw ira[i] ^ ira[i-61]; seeded with ira[j] = SplitMix64(v, j)
+ *              >> 32 for j < 61 and ira[60] made odd, v the stream's seed word)
  * Cites: Eq. 1-2 (model), Sec. 4 (threshold table), Sec. 3 (generators). */
 int isg_create(int L, uint64_t seed_J, uint64_t seed_spin, double beta, int rng_kind,
                isg_sim **out);

@@ -20,8 +20,8 @@ LIB_PATH = os.path.join(_PKG, "libisg.so")
 
 ISG_OK, ISG_ERR_ARG, ISG_ERR_NOMEM, ISG_ERR_CUDA, ISG_ERR_TIMEOUT, ISG_ERR_MISMATCH, ISG_ERR_STATE = \
     0, -1, -2, -3, -4, -5, -6
-ISG_RNG_MINSTD, ISG_RNG_MT19937 = 0, 1
-RNG_KINDS = {"minstd": ISG_RNG_MINSTD, "mt19937": ISG_RNG_MT19937}
+ISG_RNG_MINSTD, ISG_RNG_MT19937, ISG_RNG_PARISI_RAPUANO = 0, 1, 2
+RNG_KINDS = {"minstd": ISG_RNG_MINSTD, "mt19937": ISG_RNG_MT19937, "parisi_rapuano": ISG_RNG_PARISI_RAPUANO}
 
 _vp, _i32, _i64, _u64, _dbl, _sz = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64,
                                     ctypes.c_double, ctypes.c_size_t)

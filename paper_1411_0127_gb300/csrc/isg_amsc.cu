@@ -180,6 +180,9 @@ __global__ void __launch_bounds__(kAmscWarps * 32) amsc_kernel(AmscArgs a, FlipA
             uint32_t d[4];
             if (KIND == ISG_RNG_MT19937) {
                 mt_quad<kAmscSlack>(B, st.iA, d, k.mul, lane);
+            } else if (KIND == ISG_RNG_PARISI_RAPUANO) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) d[j] = pr_warp_step(st.xA, st.xB, lane, 32);
             } else {
                 d[0] = st.xA;
                 d[1] = st.xB;
@@ -196,6 +199,8 @@ __global__ void __launch_bounds__(kAmscWarps * 32) amsc_kernel(AmscArgs a, FlipA
             uint32_t d;
             if (KIND == ISG_RNG_MT19937) {
                 d = mt_single<kAmscSlack>(B, st.iA, lane, nvalid, k.mul);
+            } else if (KIND == ISG_RNG_PARISI_RAPUANO) {
+                d = pr_warp_step(st.xA, st.xB, lane, nvalid);
             } else {
                 d = st.xA;
                 const int src = lane + nvalid;
@@ -323,7 +328,7 @@ int isg_amsc_create(int L, const uint64_t* seed_J, const uint64_t* seed_spin, ui
     *out = nullptr;
     if (L < 4 || L > 1024 || (L & 1)) { set_error("isg_amsc_create: L=%d must be even and in [4, 1024]", L); return ISG_ERR_ARG; }
     if (!(beta > 0.0)) { set_error("isg_amsc_create: beta must be > 0 (got %g)", beta); return ISG_ERR_ARG; }
-    if (rng_kind != ISG_RNG_MINSTD && rng_kind != ISG_RNG_MT19937) {
+    if (!rng_kind_valid(rng_kind)) {
         set_error("isg_amsc_create: unknown rng_kind %d", rng_kind);
         return ISG_ERR_ARG;
     }
@@ -347,7 +352,7 @@ int isg_amsc_create(int L, const uint64_t* seed_J, const uint64_t* seed_spin, ui
         m->S = (m->rows + m->R - 1) / m->R;
     }
     m->plane_words = (m->rows * m->half + 63) / 64 * 64;
-    const size_t rng_words = rng_kind == ISG_RNG_MT19937 ? (size_t)m->S * kMtN : (size_t)m->S;
+    const size_t rng_words = (size_t)m->S * rng_state_words(rng_kind);
     cudaError_t e = cudaMalloc(&m->planes, (size_t)m->plane_words * 8 * 4);
     if (e == cudaSuccess) e = cudaMalloc(&m->rng, rng_words * 4);
     if (e == cudaSuccess) e = cudaMalloc(&m->rng_pos, (size_t)m->S * 4);
@@ -409,7 +414,7 @@ int isg_amsc_sweep(isg_amsc* m, int64_t n, void* cuda_stream) {
     a.R = m->R;
     a.S = m->S;
     a.rows = m->rows;
-    if (m->kind == ISG_RNG_MT19937) {
+    if (m->kind != ISG_RNG_MINSTD) {
         a.cmp1 = m->thr[1];
         a.cmp2 = m->thr[2];
         a.cmp3 = m->thr[3];
@@ -419,15 +424,15 @@ int isg_amsc_sweep(isg_amsc* m, int64_t n, void* cuda_stream) {
         a.cmp3 = (uint32_t)(((uint64_t)m->thr[3] + 1) / 2);
     }
     const size_t smem = m->kind == ISG_RNG_MT19937 ? (size_t)kAmscWarps * mt_window(kAmscSlack) * 4 : 0;
-    static int occ[2] = {0, 0};
+    static int occ[3] = {0, 0, 0};
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (!occ[m->kind]) {
-        if (m->kind == ISG_RNG_MT19937)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], amsc_kernel<ISG_RNG_MT19937>, kAmscWarps * 32, smem);
-        else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], amsc_kernel<ISG_RNG_MINSTD>, kAmscWarps * 32, smem);
+        with_kind(m->kind, [&](auto kc) {
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[m->kind], amsc_kernel<decltype(kc)::value>,
+                                                                 kAmscWarps * 32, smem);
+        });
         if (occ[m->kind] < 1) occ[m->kind] = 1;
     }
     int64_t blocks = (int64_t)sms * occ[m->kind];
@@ -436,11 +441,11 @@ int isg_amsc_sweep(isg_amsc* m, int64_t n, void* cuda_stream) {
     for (int64_t sw = 0; sw < n; ++sw) {
         for (int c = 0; c < 2; ++c) {
             a.c = c;
-            if (m->kind == ISG_RNG_MT19937)
-                amsc_kernel<ISG_RNG_MT19937><<<(unsigned)blocks, kAmscWarps * 32, smem, s>>>(a, gen, k, m->ctr, m->tickets);
-            else
-                amsc_kernel<ISG_RNG_MINSTD><<<(unsigned)blocks, kAmscWarps * 32, smem, s>>>(a, gen, k, m->ctr, m->tickets);
-            const cudaError_t e = cudaGetLastError();
+            const cudaError_t e = with_kind(m->kind, [&](auto kc) {
+                amsc_kernel<decltype(kc)::value><<<(unsigned)blocks, kAmscWarps * 32, smem, s>>>(a, gen, k, m->ctr,
+                                                                                                  m->tickets);
+                return cudaGetLastError();
+            });
             if (e != cudaSuccess) return cuda_fail(e, "isg_amsc_sweep");
             m->tickets += (unsigned long long)m->S + (unsigned long long)blocks * kAmscWarps;
         }

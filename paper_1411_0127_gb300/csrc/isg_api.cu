@@ -74,7 +74,7 @@ static int alloc_sim(isg_sim* h) {
     h->plane_bytes = (raw + 255) / 256 * 256;
     const size_t pbytes = (size_t)h->plane_bytes * 8;
     h->planes = (unsigned char*)dev_alloc(h, pbytes);
-    const size_t rng_words = h->kind == ISG_RNG_MT19937 ? (size_t)h->S * kMtN : (size_t)h->S;
+    const size_t rng_words = (size_t)h->S * rng_state_words(h->kind);
     h->rng = (uint32_t*)dev_alloc(h, rng_words * 4);
     h->rng_pos = (uint32_t*)dev_alloc(h, (size_t)h->S * 4);
     h->scal = (long long*)dev_alloc(h, 8 * sizeof(long long));
@@ -138,7 +138,7 @@ int create_sim(int L, uint64_t seed_J, uint64_t seed_spin, uint64_t seed_rng, do
     *out = nullptr;
     if (L < 4 || L > 2048 || (L & 1)) { set_error("isg_create: L=%d must be even and in [4, 2048]", L); return ISG_ERR_ARG; }
     if (!beta_ok(beta)) { set_error("isg_create: beta must be > 0 (got %g)", beta); return ISG_ERR_ARG; }
-    if (rng_kind != ISG_RNG_MINSTD && rng_kind != ISG_RNG_MT19937) {
+    if (!rng_kind_valid(rng_kind)) {
         set_error("isg_create: unknown rng_kind %d", rng_kind);
         return ISG_ERR_ARG;
     }
@@ -175,7 +175,7 @@ size_t sim_device_bytes(int L, int rng_kind, bool force32) {
     int64_t R = 0, S = 0;
     partition(L, &R, &S);
     const int64_t plane = (rows * W * (wbits / 8) + 255) / 256 * 256;
-    const int64_t rng = rng_kind == ISG_RNG_MT19937 ? S * kMtN * 4 : S * 4;
+    const int64_t rng = S * rng_state_words(rng_kind) * 4;
     return (size_t)(8 * plane + rng + S * 4 + 8 * (int64_t)sizeof(long long));
 }
 
@@ -377,7 +377,7 @@ static const char kMagic[8] = {'I', 'S', 'G', 'C', 'K', 'P', 'T', '2'};
 
 int isg_save(const isg_sim* h, void* buf, size_t* n, void* stream) {
     if (!h || !n) { set_error("isg_save: NULL argument"); return ISG_ERR_ARG; }
-    const size_t rng_words = h->kind == ISG_RNG_MT19937 ? (size_t)h->S * kMtN : (size_t)h->S;
+    const size_t rng_words = (size_t)h->S * rng_state_words(h->kind);
     const size_t need = sizeof(SaveHeader) + (size_t)h->plane_bytes * 8 + rng_words * 4 + (size_t)h->S * 4;
     if (!buf) { *n = need; return ISG_OK; }
     if (*n < need) { *n = need; set_error("isg_save: buffer too small"); return ISG_ERR_ARG; }
@@ -423,7 +423,7 @@ int isg_load(const void* buf, size_t n, isg_sim** out) {
     if (n < sizeof hd) { set_error("isg_load: truncated buffer"); return ISG_ERR_ARG; }
     memcpy(&hd, buf, sizeof hd);
     if (memcmp(hd.magic, kMagic, 8) != 0 || hd.version != 1) { set_error("isg_load: not a checkpoint"); return ISG_ERR_ARG; }
-    if (hd.L < 4 || hd.L > 2048 || (hd.L & 1) || hd.kind > 1 || !beta_ok(hd.beta)) {
+    if (hd.L < 4 || hd.L > 2048 || (hd.L & 1) || !rng_kind_valid((int)hd.kind) || !beta_ok(hd.beta)) {
         set_error("isg_load: corrupt header");
         return ISG_ERR_ARG;
     }
@@ -439,7 +439,7 @@ int isg_load(const void* buf, size_t n, isg_sim** out) {
     thresholds(h->beta, h->thr);
     int rc = alloc_sim(h);
     if (rc) { free_sim(h); return rc; }
-    const size_t rng_words = h->kind == ISG_RNG_MT19937 ? (size_t)h->S * kMtN : (size_t)h->S;
+    const size_t rng_words = (size_t)h->S * rng_state_words(h->kind);
     const size_t need = sizeof hd + (size_t)h->plane_bytes * 8 + rng_words * 4 + (size_t)h->S * 4;
     if (n < need || hd.plane_bytes != h->plane_bytes || hd.S != h->S || hd.R != h->R ||
         hd.rng_words != (int64_t)rng_words || (int)hd.wbits != h->wbits) {

@@ -117,9 +117,10 @@ static size_t batch_smem(int kind) {
 
 cudaError_t prepare_bundle_kernel(int kind) {
     const int smem = (int)batch_smem(kind);
-    return kind == ISG_RNG_MT19937
-               ? cudaFuncSetAttribute(batch_kernel<ISG_RNG_MT19937>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
-               : cudaFuncSetAttribute(batch_kernel<ISG_RNG_MINSTD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return with_kind(kind, [&](auto kc) {
+        return cudaFuncSetAttribute(batch_kernel<decltype(kc)::value>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    smem);
+    });
 }
 
 cudaError_t launch_bundle_kernel(int kind, const FlipArgs* reps, const int2* entries, const int* boff,
@@ -139,11 +140,10 @@ cudaError_t launch_bundle_kernel(int kind, const FlipArgs* reps, const int2* ent
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = std::max(1, std::min(sms, nbundles));
-    if (kind == ISG_RNG_MT19937)
-        batch_kernel<ISG_RNG_MT19937><<<grid, kBatchWarps * 32, smem, s>>>(a, k);
-    else
-        batch_kernel<ISG_RNG_MINSTD><<<grid, kBatchWarps * 32, smem, s>>>(a, k);
-    return cudaGetLastError();
+    return with_kind(kind, [&](auto kc) {
+        batch_kernel<decltype(kc)::value><<<grid, kBatchWarps * 32, smem, s>>>(a, k);
+        return cudaGetLastError();
+    });
 }
 
 void plan_bundles(const std::vector<isg_sim*>& reps, std::vector<int2>& entries, std::vector<int>& boff,
@@ -230,7 +230,7 @@ int isg_batch_create(int n, const int* L, const uint64_t* seed_J, const uint64_t
     if (!out) { set_error("isg_batch_create: out is NULL"); return ISG_ERR_ARG; }
     *out = nullptr;
     if (n < 1 || !L || !seed_J || !seed_spin || !beta) { set_error("isg_batch_create: bad argument"); return ISG_ERR_ARG; }
-    if (rng_kind != ISG_RNG_MINSTD && rng_kind != ISG_RNG_MT19937) {
+    if (!rng_kind_valid(rng_kind)) {
         set_error("isg_batch_create: unknown rng_kind %d", rng_kind);
         return ISG_ERR_ARG;
     }

@@ -11,6 +11,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "isg.h"
@@ -27,6 +28,7 @@ constexpr uint32_t kMinstdA = 16807u;
 
 constexpr int kMtN = 624;   // MT19937 state words
 constexpr int kMtM = 397;   // middle offset
+constexpr int kPrN = 61;    // Parisi-Rapuano state words (the longest lag)
 constexpr int kCondWords = 68;  // per condition plane: 2048 draw bits + padding
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
@@ -94,7 +96,7 @@ struct FlipArgs {
     int L, half, W, nt, c;
     int64_t R, S, rows;
     uint32_t thr1, thr2, thr3;
-    uint32_t cmp1, cmp2, cmp3;   // compared with the generator value: MT19937 thr_k, MINSTD ceil(thr_k / 2)
+    uint32_t cmp1, cmp2, cmp3;   // compared with the generator value: thr_k, for MINSTD ceil(thr_k / 2)
     uint32_t* rng;
     uint32_t* rng_pos;
     long long* dE;
@@ -115,6 +117,64 @@ __device__ __forceinline__ uint32_t minstd_warp_step(uint32_t& x, uint32_t a32, 
         x = src < 32 ? xa : ya;
     }
     return d;
+}
+
+// Parisi-Rapuano (Sec. 3): ira[i] = ira[i-24] + ira[i-55] (mod 2^32), draw
+// R = ira[i] ^ ira[i-61].  A warp keeps ira[i-64 .. i-1] in two registers per
+// lane, a = ira[i-64+l] and b = ira[i-32+l]; lane l makes draw i + l.  Lanes
+// 0..23 find both lags in the registers; lanes 24..31 need ira[i+l-24], made
+// by lane l-24 in the same step.  Moves every lane forward by nvalid draws.
+__device__ __forceinline__ uint32_t pr_warp_step(uint32_t& a, uint32_t& b, int lane, int nvalid) {
+    const int s3 = (lane + 3) & 31, s8 = (lane + 8) & 31, s9 = (lane + 9) & 31;
+    const uint32_t lag24 = __shfl_sync(kFull, b, s8);
+    const uint32_t a9 = __shfl_sync(kFull, a, s9), b9 = __shfl_sync(kFull, b, s9);
+    const uint32_t a3 = __shfl_sync(kFull, a, s3), b3 = __shfl_sync(kFull, b, s3);
+    const uint32_t lag55 = lane < 23 ? a9 : b9;   // ira[i+l-55]
+    const uint32_t lag61 = lane < 29 ? a3 : b3;   // ira[i+l-61]
+    const uint32_t v0 = lag24 + lag55;
+    const uint32_t v1 = __shfl_sync(kFull, v0, s8) + lag55;
+    const uint32_t v = lane < 24 ? v0 : v1;       // ira[i+l]
+    if (nvalid == 32) {
+        a = b;
+        b = v;
+    } else {
+        const int src = (lane + nvalid) & 31;
+        const bool up = lane + nvalid >= 32;
+        const uint32_t as = __shfl_sync(kFull, a, src), bs = __shfl_sync(kFull, b, src);
+        const uint32_t vs = __shfl_sync(kFull, v, src);
+        a = up ? bs : as;
+        b = up ? vs : bs;
+    }
+    return v ^ lag61;
+}
+
+// The stored Parisi-Rapuano state of a stream is ira[i-61 .. i-1], oldest
+// first (61 words); lanes 0..2 of `a` hold words that are never read.
+__device__ __forceinline__ void pr_load(const uint32_t* st, uint32_t& a, uint32_t& b, int lane) {
+    a = lane >= 3 ? st[lane - 3] : 0u;
+    b = st[29 + lane];
+}
+
+__device__ __forceinline__ void pr_store(uint32_t* st, uint32_t a, uint32_t b, int lane) {
+    if (lane >= 3) st[lane - 3] = a;
+    st[29 + lane] = b;
+}
+
+// Words of stored state per stream.
+__host__ __device__ constexpr int rng_state_words(int kind) {
+    return kind == ISG_RNG_MT19937 ? kMtN : (kind == ISG_RNG_PARISI_RAPUANO ? kPrN : 1);
+}
+
+inline bool rng_kind_valid(int kind) {
+    return kind == ISG_RNG_MINSTD || kind == ISG_RNG_MT19937 || kind == ISG_RNG_PARISI_RAPUANO;
+}
+
+// Host dispatch on the generator kind: f(std::integral_constant<int, KIND>).
+template <class F>
+inline auto with_kind(int kind, F&& f) {
+    if (kind == ISG_RNG_MT19937) return f(std::integral_constant<int, ISG_RNG_MT19937>{});
+    if (kind == ISG_RNG_PARISI_RAPUANO) return f(std::integral_constant<int, ISG_RNG_PARISI_RAPUANO>{});
+    return f(std::integral_constant<int, ISG_RNG_MINSTD>{});
 }
 
 // ---------------------------------------------------------------------------

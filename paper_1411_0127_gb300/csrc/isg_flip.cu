@@ -19,6 +19,8 @@ namespace isg {
 
 constexpr int kFlipWarps = 4;
 
+// Shared-memory words of one warp's generator state: MT19937 keeps its
+// 624-word ring there; MINSTD and Parisi-Rapuano live in registers.
 template <int KIND>
 struct RingWords {
     static constexpr int value = (KIND == ISG_RNG_MT19937) ? kMtN : 0;
@@ -91,11 +93,13 @@ __global__ void __launch_bounds__(kFlipWarps * 32) flip_plain_kernel(FlipArgs a)
     uint32_t* cond = ring + kRing;
 
     int pos = 0;
-    uint32_t x = 0;
+    uint32_t x = 0, x2 = 0;
     if (KIND == ISG_RNG_MT19937) {
         for (int i = lane; i < kMtN; i += 32) ring[i] = a.rng[t * kMtN + i];
         pos = (int)a.rng_pos[t];
         __syncwarp();
+    } else if (KIND == ISG_RNG_PARISI_RAPUANO) {
+        pr_load(a.rng + t * kPrN, x, x2, lane);
     } else {
         x = minstd_mulmod(a.rng[t], a.mt.pow[lane + 1]);
     }
@@ -113,6 +117,7 @@ __global__ void __launch_bounds__(kFlipWarps * 32) flip_plain_kernel(FlipArgs a)
             const int nvalid = D - 32 * b < 32 ? D - 32 * b : 32;
             uint32_t d;
             if (KIND == ISG_RNG_MT19937) d = mt_warp_step(ring, pos, lane, nvalid);
+            else if (KIND == ISG_RNG_PARISI_RAPUANO) d = pr_warp_step(x, x2, lane, nvalid);
             else d = minstd_warp_step(x, a.mt.pow[32], nvalid, lane);
             const uint32_t m4 = __ballot_sync(kFull, d < a.thr1);
             const uint32_t m8 = __ballot_sync(kFull, d < a.thr2);
@@ -131,6 +136,8 @@ __global__ void __launch_bounds__(kFlipWarps * 32) flip_plain_kernel(FlipArgs a)
     if (KIND == ISG_RNG_MT19937) {
         for (int i = lane; i < kMtN; i += 32) a.rng[t * kMtN + i] = ring[i];
         if (lane == 0) a.rng_pos[t] = (uint32_t)pos;
+    } else if (KIND == ISG_RNG_PARISI_RAPUANO) {
+        pr_store(a.rng + t * kPrN, x, x2, lane);
     } else {
         const uint32_t x0 = __shfl_sync(kFull, x, 0);
         if (lane == 0) a.rng[t] = minstd_mulmod(x0, a.mt.inv);  // state of the last draw used
@@ -168,7 +175,7 @@ FlipArgs make_flip_args(isg_sim* h, int colour) {
     a.thr1 = h->thr[1];
     a.thr2 = h->thr[2];
     a.thr3 = h->thr[3];
-    if (h->kind == ISG_RNG_MT19937) {
+    if (h->kind != ISG_RNG_MINSTD) {
         a.cmp1 = h->thr[1];
         a.cmp2 = h->thr[2];
         a.cmp3 = h->thr[3];
@@ -194,11 +201,10 @@ static cudaError_t launch_plain_t(isg_sim* h, int colour, cudaStream_t s) {
 }
 
 cudaError_t launch_flip_plain(isg_sim* h, int colour, cudaStream_t s) {
-    if (h->wbits == 64)
-        return h->kind == ISG_RNG_MT19937 ? launch_plain_t<uint64_t, ISG_RNG_MT19937>(h, colour, s)
-                                          : launch_plain_t<uint64_t, ISG_RNG_MINSTD>(h, colour, s);
-    return h->kind == ISG_RNG_MT19937 ? launch_plain_t<uint32_t, ISG_RNG_MT19937>(h, colour, s)
-                                      : launch_plain_t<uint32_t, ISG_RNG_MINSTD>(h, colour, s);
+    return with_kind(h->kind, [&](auto kind) {
+        constexpr int K = decltype(kind)::value;
+        return h->wbits == 64 ? launch_plain_t<uint64_t, K>(h, colour, s) : launch_plain_t<uint32_t, K>(h, colour, s);
+    });
 }
 
 // ---------------------------------------------------------------------------
@@ -209,29 +215,32 @@ __global__ void peek_kernel(const uint32_t* rng, const uint32_t* rng_pos, int64_
     __shared__ uint32_t ring[kMtN];
     const int lane = threadIdx.x;
     int pos = 0;
-    uint32_t x = 0;
+    uint32_t x = 0, x2 = 0;
     if (KIND == ISG_RNG_MT19937) {
         for (int i = lane; i < kMtN; i += 32) ring[i] = rng[t * kMtN + i];
         pos = (int)rng_pos[t];
         __syncwarp();
+    } else if (KIND == ISG_RNG_PARISI_RAPUANO) {
+        pr_load(rng + t * kPrN, x, x2, lane);
     } else {
         x = minstd_mulmod(rng[t], mt.pow[lane + 1]);
     }
     for (int64_t k = 0; k < n; k += 32) {
         const int nvalid = n - k < 32 ? (int)(n - k) : 32;
-        uint32_t d = KIND == ISG_RNG_MT19937 ? mt_warp_step(ring, pos, lane, nvalid)
-                                             : minstd_warp_step(x, mt.pow[32], nvalid, lane);
+        uint32_t d;
+        if (KIND == ISG_RNG_MT19937) d = mt_warp_step(ring, pos, lane, nvalid);
+        else if (KIND == ISG_RNG_PARISI_RAPUANO) d = pr_warp_step(x, x2, lane, nvalid);
+        else d = minstd_warp_step(x, mt.pow[32], nvalid, lane);
         if (lane < nvalid) out[k + lane] = d;
     }
 }
 
 cudaError_t launch_peek_draws(const isg_sim* h, int64_t t, int64_t n, uint32_t* out, cudaStream_t s) {
     const MinstdTable mt = minstd_table();
-    if (h->kind == ISG_RNG_MT19937)
-        peek_kernel<ISG_RNG_MT19937><<<1, 32, 0, s>>>(h->rng, h->rng_pos, t, n, out, mt);
-    else
-        peek_kernel<ISG_RNG_MINSTD><<<1, 32, 0, s>>>(h->rng, h->rng_pos, t, n, out, mt);
-    return cudaGetLastError();
+    return with_kind(h->kind, [&](auto kind) {
+        peek_kernel<decltype(kind)::value><<<1, 32, 0, s>>>(h->rng, h->rng_pos, t, n, out, mt);
+        return cudaGetLastError();
+    });
 }
 
 // ---------------------------------------------------------------------------

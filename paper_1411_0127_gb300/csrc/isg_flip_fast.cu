@@ -52,7 +52,7 @@ static cudaError_t launch_fast_t(isg_sim* h, int colour, cudaStream_t s) {
     constexpr int kRing = KIND == ISG_RNG_MT19937 ? mt_window(kFastSlack) : 0;
     const size_t smem = (size_t)kFastWarps * (kRing + 2 * kCondWords) * sizeof(uint32_t);
     static int sms = 0;
-    static int per_sm[2][2] = {{0, 0}, {0, 0}};
+    static int per_sm[2][3] = {{0, 0, 0}, {0, 0, 0}};
     int& occ = per_sm[sizeof(Word) == 8][KIND];
     if (sms == 0) {
         int dev = 0;
@@ -75,11 +75,10 @@ static cudaError_t launch_fast_t(isg_sim* h, int colour, cudaStream_t s) {
 }
 
 cudaError_t launch_flip_fast(isg_sim* h, int colour, cudaStream_t s) {
-    if (h->wbits == 64)
-        return h->kind == ISG_RNG_MT19937 ? launch_fast_t<uint64_t, ISG_RNG_MT19937>(h, colour, s)
-                                          : launch_fast_t<uint64_t, ISG_RNG_MINSTD>(h, colour, s);
-    return h->kind == ISG_RNG_MT19937 ? launch_fast_t<uint32_t, ISG_RNG_MT19937>(h, colour, s)
-                                      : launch_fast_t<uint32_t, ISG_RNG_MINSTD>(h, colour, s);
+    return with_kind(h->kind, [&](auto kind) {
+        constexpr int K = decltype(kind)::value;
+        return h->wbits == 64 ? launch_fast_t<uint64_t, K>(h, colour, s) : launch_fast_t<uint32_t, K>(h, colour, s);
+    });
 }
 
 }  // namespace isg

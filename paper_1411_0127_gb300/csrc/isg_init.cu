@@ -4,7 +4,9 @@
 // is set; spins: s_i = -1 when bit 63 of SplitMix64(seed_spin ^ K_S, i) is set.
 // Streams: v_t = SplitMix64(seed_rng ^ K_R, t) (seed_rng = seed_spin unless the
 // handle was made with isg_create2); MT19937 starts from
-// init_genrand((uint32) v_t), MINSTD from x_0 = 1 + v_t mod (2^31 - 2) (Sec. 3).
+// init_genrand((uint32) v_t), MINSTD from x_0 = 1 + v_t mod (2^31 - 2), and
+// Parisi-Rapuano from ira[j] = SplitMix64(v_t, j) >> 32, j < 61, with ira[60]
+// made odd (Sec. 3).
 #include "isg_common.cuh"
 
 namespace isg {
@@ -91,6 +93,10 @@ __global__ void init_rng_kernel(int kind, uint64_t seed_rng, int64_t S, uint32_t
             x[k] = prev;
         }
         pos[t] = 0;
+    } else if (kind == ISG_RNG_PARISI_RAPUANO) {
+        uint32_t* w = rng + t * kPrN;
+        for (int j = 0; j < kPrN; ++j) w[j] = (uint32_t)(splitmix64(v, (uint64_t)j) >> 32);
+        w[kPrN - 1] |= 1u;
     } else {
         rng[t] = 1u + (uint32_t)(v % 2147483646ull);
     }

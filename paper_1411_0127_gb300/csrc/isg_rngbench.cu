@@ -3,9 +3,10 @@
 //
 // `streams` streams of one kind are seeded exactly like the streams of a lattice
 // (v_t = SplitMix64(seed ^ K_R, t); MT19937 init_genrand((uint32) v_t), MINSTD
-// x_0 = 1 + v_t mod (2^31 - 2)).  Each warp then produces n consecutive raw
-// outputs of its stream with the same engines the flip kernels use (MT19937:
-// tempered word; MINSTD: the state x itself) and counts the odd ones.
+// x_0 = 1 + v_t mod (2^31 - 2); Parisi-Rapuano ira[j] = SplitMix64(v_t, j) >> 32).
+// Each warp then produces n consecutive raw outputs of its stream with the same
+// engines the flip kernels use (MT19937: tempered word; MINSTD: the state x
+// itself; Parisi-Rapuano: ira[i] ^ ira[i-61]) and counts the odd ones.
 #include "isg_stream.cuh"
 
 namespace isg {
@@ -27,6 +28,8 @@ __global__ void __launch_bounds__(kBenchWarps * 32) rng_odd_kernel(const uint32_
         if (KIND == ISG_RNG_MT19937) {
             for (int j = lane; j < kMtN; j += 32) B[j] = state[t * kMtN + j];
             __syncwarp();
+        } else if (KIND == ISG_RNG_PARISI_RAPUANO) {
+            pr_load(state + t * kPrN, xA, xB, lane);
         } else {
             xA = minstd_mulmod(state[t], mt.pow[lane + 1]);
             xB = minstd_mulmod(xA, k.a32);
@@ -42,6 +45,16 @@ __global__ void __launch_bounds__(kBenchWarps * 32) rng_odd_kernel(const uint32_
             for (; done < n; done += 32) {
                 const int nvalid = n - done < 32 ? (int)(n - done) : 32;
                 const uint32_t d = mt_single<kBenchSlack>(B, iA, lane, nvalid, k.mul);
+                cnt += __popc(__ballot_sync(kFull, (d & 1u) && lane < nvalid));
+            }
+        } else if (KIND == ISG_RNG_PARISI_RAPUANO) {
+            for (; done + 128 <= n; done += 128) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) cnt += __popc(__ballot_sync(kFull, pr_warp_step(xA, xB, lane, 32) & 1u));
+            }
+            for (; done < n; done += 32) {
+                const int nvalid = n - done < 32 ? (int)(n - done) : 32;
+                const uint32_t d = pr_warp_step(xA, xB, lane, nvalid);
                 cnt += __popc(__ballot_sync(kFull, (d & 1u) && lane < nvalid));
             }
         } else {
@@ -68,11 +81,11 @@ using namespace isg;
 
 extern "C" int isg_rng_count_odd(int rng_kind, uint64_t seed, int64_t streams, int64_t n, uint64_t* odd,
                                  double* gen_ms) {
-    if (!odd || streams < 1 || n < 0 || (rng_kind != ISG_RNG_MINSTD && rng_kind != ISG_RNG_MT19937)) {
+    if (!odd || streams < 1 || n < 0 || !rng_kind_valid(rng_kind)) {
         set_error("isg_rng_count_odd: bad argument");
         return ISG_ERR_ARG;
     }
-    const size_t words = rng_kind == ISG_RNG_MT19937 ? (size_t)streams * kMtN : (size_t)streams;
+    const size_t words = (size_t)streams * rng_state_words(rng_kind);
     uint32_t *state = nullptr, *pos = nullptr;
     unsigned long long* dodd = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -104,11 +117,10 @@ extern "C" int isg_rng_count_odd(int rng_kind, uint64_t seed, int64_t streams, i
         const int64_t need = (streams + kBenchWarps - 1) / kBenchWarps;
         const unsigned grid = (unsigned)(need < (int64_t)sms * 16 ? need : (int64_t)sms * 16);
         cudaEventRecord(e0, 0);
-        if (rng_kind == ISG_RNG_MT19937)
-            rng_odd_kernel<ISG_RNG_MT19937><<<grid, kBenchWarps * 32, smem, 0>>>(state, streams, n, mt, k, dodd);
-        else
-            rng_odd_kernel<ISG_RNG_MINSTD><<<grid, kBenchWarps * 32, smem, 0>>>(state, streams, n, mt, k, dodd);
-        e = cudaGetLastError();
+        e = with_kind(rng_kind, [&](auto kc) {
+            rng_odd_kernel<decltype(kc)::value><<<grid, kBenchWarps * 32, smem, 0>>>(state, streams, n, mt, k, dodd);
+            return cudaGetLastError();
+        });
         cudaEventRecord(e1, 0);
     }
     unsigned long long h = 0;

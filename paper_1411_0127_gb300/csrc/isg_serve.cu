@@ -31,6 +31,7 @@
 namespace isg {
 
 constexpr int kWideStreams = 8;
+constexpr int kKinds = 3;   // generator kinds: one bundle plan and stream each
 constexpr int64_t kBatchedMaxStreams = 256;
 
 struct ServeJob {
@@ -69,8 +70,8 @@ struct isg_server {
     int max_active = 4096;
     std::mutex mu;
     std::vector<isg::ServeJob> jobs;
-    isg::PlanBuf plan[2];
-    cudaStream_t batch_stream[2] = {nullptr, nullptr};
+    isg::PlanBuf plan[isg::kKinds];
+    cudaStream_t batch_stream[isg::kKinds] = {nullptr, nullptr, nullptr};
     cudaStream_t wide_stream[isg::kWideStreams] = {};
     // statistics of the last run
     int64_t iterations = 0, attempts = 0;
@@ -183,7 +184,7 @@ int isg_server_create(size_t hbm_budget_bytes, int quantum_sweeps, int max_activ
     s->quantum = quantum_sweeps > 0 ? quantum_sweeps : 64;
     s->max_active = max_active > 0 ? max_active : 4096;
     cudaError_t e = cudaSuccess;
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    for (int k = 0; k < kKinds && e == cudaSuccess; ++k) {
         e = cudaStreamCreateWithFlags(&s->batch_stream[k], cudaStreamNonBlocking);
         if (e == cudaSuccess) {
             s->plan[k].ctr = (unsigned*)g_dev_alloc(2 * sizeof(unsigned));
@@ -224,7 +225,7 @@ void isg_server_destroy(isg_server* s) {
 int isg_server_submit(isg_server* s, int L, uint64_t seed_J, uint64_t seed_spin, double beta, int rng_kind,
                       int64_t sweeps, double arrival_s, int64_t* job_id) {
     if (!s || !job_id || sweeps < 0 || L < 4 || L > 2048 || (L & 1) || !(beta > 0.0) ||
-        (rng_kind != ISG_RNG_MINSTD && rng_kind != ISG_RNG_MT19937) || !(arrival_s >= 0.0)) {
+        !rng_kind_valid(rng_kind) || !(arrival_s >= 0.0)) {
         set_error("isg_server_submit: bad argument (L=%d beta=%g kind=%d sweeps=%lld)", L, beta, rng_kind,
                   (long long)sweeps);
         return ISG_ERR_ARG;
@@ -321,11 +322,11 @@ int isg_server_run(isg_server* s, double time_limit_s) {
             J.done += q;
             s->attempts += q * (int64_t)J.L * J.L * J.L;
         }
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < kKinds; ++k) {
             const int rc = launch_batched(s, k, active);
             if (rc) return rc;
         }
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < kKinds; ++k) {
             const int rc = finish_batched(s, k);
             if (rc) return rc;
         }

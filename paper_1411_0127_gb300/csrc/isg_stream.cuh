@@ -26,7 +26,9 @@
 //     pipe;
 //   * MINSTD keeps two lanes' worth of states (positions +1..+32 and +33..+64)
 //     and compares the state x with ceil(thr / 2) (d = 2x < thr <=> x <
-//     ceil(thr / 2)).
+//     ceil(thr / 2));
+//   * Parisi-Rapuano keeps its 64-word window in two registers per lane
+//     (pr_warp_step in isg_common.cuh): no shared memory.
 #pragma once
 
 #include "isg_common.cuh"
@@ -212,8 +214,8 @@ __device__ __forceinline__ void word_update(const FlipArgs& a, int c, int r, int
 struct StreamRegs {
     int pos;       // MT19937: position (mod 624) of the next draw in the stored ring
     int iA;        // MT19937: window index of x_k for the next draw k
-    uint32_t xA;   // MINSTD: state of draw n + lane + 1
-    uint32_t xB;   // MINSTD: state of draw n + lane + 33
+    uint32_t xA;   // MINSTD: state of draw n + lane + 1; Parisi-Rapuano: ira[i-64+lane]
+    uint32_t xB;   // MINSTD: state of draw n + lane + 33; Parisi-Rapuano: ira[i-32+lane]
 };
 
 // The stored MT19937 state is a 624-word ring with the position of the next
@@ -231,6 +233,8 @@ __device__ __forceinline__ void load_stream(const FlipArgs& a, int64_t t, uint32
         st.pos = p;
         st.iA = 0;
         __syncwarp();
+    } else if (KIND == ISG_RNG_PARISI_RAPUANO) {
+        pr_load(a.rng + t * kPrN, st.xA, st.xB, lane);
     } else {
         st.xA = minstd_mulmod(a.rng[t], a.mt.pow[lane + 1]);
         st.xB = minstd_mulmod(st.xA, k.a32);
@@ -248,6 +252,8 @@ __device__ __forceinline__ void store_stream(const FlipArgs& a, int64_t t, const
         }
         if (lane == 0) a.rng_pos[t] = (uint32_t)st.pos;
         __syncwarp();
+    } else if (KIND == ISG_RNG_PARISI_RAPUANO) {
+        pr_store(a.rng + t * kPrN, st.xA, st.xB, lane);
     } else {
         const uint32_t x0 = __shfl_sync(kFull, st.xA, 0);
         if (lane == 0) a.rng[t] = minstd_mulmod(x0, a.mt.inv);  // state of the last draw used
@@ -295,6 +301,22 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t t,
                 }
             }
             b = 4 * nquads;
+        } else if (KIND == ISG_RNG_PARISI_RAPUANO) {
+            const int nquads = D >> 7;
+            for (int q = 0; q < nquads; ++q) {
+                uint32_t lo[4], hi[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t d = pr_warp_step(st.xA, st.xB, lane, 32);
+                    lo[j] = __ballot_sync(kFull, level_lo(d, a));
+                    hi[j] = __ballot_sync(kFull, d < a.cmp2);
+                }
+                if (lane == 0) {
+                    *(uint4*)(cond + 4 * q) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                    *(uint4*)(cond + kCondWords + 4 * q) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                }
+            }
+            b = 4 * nquads;
         } else {
             const int npairs = D >> 6;
             for (int q = 0; q < npairs; ++q) {
@@ -316,6 +338,8 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t t,
             uint32_t d;
             if (kMT) {
                 d = mt_single<SLACK>(B, st.iA, lane, nvalid, k.mul);
+            } else if (KIND == ISG_RNG_PARISI_RAPUANO) {
+                d = pr_warp_step(st.xA, st.xB, lane, nvalid);
             } else {
                 d = st.xA;
                 const int src = lane + nvalid;

@@ -53,7 +53,7 @@ def test_amsc_create_rejects_bad_arguments_without_touching_the_device(isg):
     lib = isg.lib()
     seeds = (ctypes.c_uint64 * 32)(*range(32))
     for L, beta, kind in [(5, 1.0, 0), (2, 1.0, 0), (1026, 1.0, 0), (8, 0.0, 0), (8, -1.0, 1),
-                          (8, float("nan"), 0), (8, 1.0, 2)]:
+                          (8, float("nan"), 0), (8, 1.0, 3)]:
         assert lib.isg_amsc_create(L, seeds, seeds, 3, beta, kind, ctypes.byref(h)) == isg.ISG_ERR_ARG
         assert h.value is None
     assert lib.isg_amsc_create(8, None, seeds, 3, 1.0, 0, ctypes.byref(h)) == isg.ISG_ERR_ARG

@@ -47,6 +47,8 @@ def oracles(L, J, S, R, beta, kind):
     (12, "mt19937", math.inf, 5, 1),
     (50, "minstd", 1 / 0.9, 4, 2),
     (64, "mt19937", 1 / 0.9, 3, 3),
+    (10, "parisi_rapuano", 1 / 0.8, 6, 2),
+    (50, "parisi_rapuano", 1 / 1.1, 4, 4),
 ])
 def test_every_system_matches_its_lone_lattice(isg, L, kind, beta, sweeps, every):
     J, S = seeds(L)

@@ -37,7 +37,7 @@ def mixed(n_per_size=1, temps=(0.7, 1.1)):
     return L, J, S, B
 
 
-@pytest.mark.parametrize("kind", ["mt19937", "minstd"])
+@pytest.mark.parametrize("kind", ["mt19937", "minstd", "parisi_rapuano"])
 def test_batch_matches_oracle(isg, kind):
     L, J, S, B = mixed()
     b = isg.Batch(L, J, S, B, kind)

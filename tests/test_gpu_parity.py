@@ -16,6 +16,17 @@ from oracle import OracleSim
 pytestmark = pytest.mark.gpu
 
 K_STREAMS = 0x3C6EF372FE94F82B
+KINDS = ["minstd", "mt19937", "parisi_rapuano"]
+
+
+def raw_outputs(kind, v, n):
+    """The oracle's raw outputs of a stream with seed word v, as the kernels
+    compare them: MT19937 and Parisi-Rapuano as is, MINSTD doubled."""
+    if kind == "mt19937":
+        return oracle.mt19937_outputs(v & 0xFFFFFFFF, n)
+    if kind == "parisi_rapuano":
+        return oracle.pr_outputs(v, n)
+    return (oracle.minstd_outputs(1 + v % (2**31 - 2), n) << 1).astype(np.uint32)
 
 
 @pytest.fixture(scope="module")
@@ -59,16 +70,14 @@ def test_stencil_logic_exhaustive(isg):
 
 # ---------------------------------------------------------------- streams ---
 
-@pytest.mark.parametrize("kind", ["minstd", "mt19937"])
+@pytest.mark.parametrize("kind", KINDS)
 def test_stream_draws(isg, kind):
     g, o = pair(isg, 96, kind, 1.0)                 # 27 streams
     for t in (0, 1, 13, 26):
         assert np.array_equal(g.peek_draws(t, 5000), o.peek_draws(t, 5000)), t
     # independently of the oracle's stream set-up: the library generators
     v = oracle.splitmix64(2 ^ K_STREAMS, 5)
-    ref = (oracle.mt19937_outputs(v & 0xFFFFFFFF, 3000) if kind == "mt19937"
-           else (oracle.minstd_outputs(1 + v % (2**31 - 2), 3000) << 1).astype(np.uint32))
-    assert np.array_equal(g.peek_draws(5, 3000), ref)
+    assert np.array_equal(g.peek_draws(5, 3000), raw_outputs(kind, v, 3000))
     # after sweeps the streams continue where the oracle's do
     g.sweep(2)
     o.sweep(2)
@@ -76,7 +85,7 @@ def test_stream_draws(isg, kind):
         assert np.array_equal(g.peek_draws(t, 777), o.peek_draws(t, 777))
 
 
-@pytest.mark.parametrize("kind", ["minstd", "mt19937"])
+@pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("n", [1000, 4096, 20001])
 def test_generator_benchmark_counts(isg, kind, n):
     """The device-API benchmark (odd outputs) against the oracle's generators,
@@ -86,8 +95,8 @@ def test_generator_benchmark_counts(isg, kind, n):
     ref = 0
     for t in range(streams):
         v = oracle.splitmix64(seed ^ K_STREAMS, t)
-        out = (oracle.mt19937_outputs(v & 0xFFFFFFFF, n) if kind == "mt19937"
-               else oracle.minstd_outputs(1 + v % (2**31 - 2), n))
+        out = (oracle.minstd_outputs(1 + v % (2**31 - 2), n) if kind == "minstd"   # the state x itself
+               else raw_outputs(kind, v, n))
         ref += int((out & 1).sum())
     assert odd == ref
     assert ms >= 0.0
@@ -109,7 +118,7 @@ def test_initial_state(isg, L):
 RAGGED = [4, 6, 8, 10, 14, 18, 34, 46, 62, 66, 94, 98, 130, 192]
 
 
-@pytest.mark.parametrize("kind", ["minstd", "mt19937"])
+@pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("L", RAGGED)
 def test_trajectory_ragged_sizes(isg, L, kind):
     g, o = pair(isg, L, kind, 1 / 1.1, seed_J=L, seed_spin=3 * L + 1)
@@ -125,7 +134,7 @@ def test_trajectory_ragged_sizes(isg, L, kind):
 
 @pytest.mark.parametrize("beta", [math.inf, 1e-9, 0.05, 3.0])
 def test_trajectory_extreme_temperatures(isg, beta):
-    for kind in ("minstd", "mt19937"):
+    for kind in KINDS:
         g, o = pair(isg, 20, kind, beta)
         g.sweep(5)
         o.sweep(5)
@@ -148,7 +157,7 @@ def test_small_workload_every_sweep(isg):
     assert np.array_equal(g.read_spins(), o.spins())
 
 
-@pytest.mark.parametrize("kind", ["minstd", "mt19937"])
+@pytest.mark.parametrize("kind", KINDS)
 def test_medium_workload_powers_of_two(isg, kind):
     """L = 256, T = 0.7: energy and hash at sweeps 2^k, k = 0..10."""
     g, o = pair(isg, 256, kind, 1 / 0.7)
@@ -179,7 +188,7 @@ def test_large_workload_two_sweeps(isg):
 
 # ------------------------------------------------------------- invariants ---
 
-@pytest.mark.parametrize("kind", ["minstd", "mt19937"])
+@pytest.mark.parametrize("kind", KINDS)
 def test_tracked_energy_long_run(isg, kind):
     g = isg.Sim(128, 9, 10, 1 / 0.9, kind)
     for _ in range(5):
@@ -195,7 +204,7 @@ def test_plain_and_default_sweep_agree(isg):
     assert a.hash() == b.hash() and a.tracked_energy() == b.tracked_energy()
 
 
-@pytest.mark.parametrize("kind", ["minstd", "mt19937"])
+@pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("L", [6, 48, 98, 256])
 def test_fast_and_plain_kernels_interleaved(isg, L, kind):
     """The two flip kernels share the stream-state format: alternating them on
@@ -264,7 +273,7 @@ def test_overlap(isg):
 
 # --------------------------------------------------------------- plumbing ---
 
-@pytest.mark.parametrize("kind", ["minstd", "mt19937"])
+@pytest.mark.parametrize("kind", KINDS)
 def test_checkpoint_resume(isg, kind):
     a = isg.Sim(48, 3, 4, 1 / 0.9, kind)
     a.sweep(5)

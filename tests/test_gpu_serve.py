@@ -29,7 +29,7 @@ def trace(n=28, seed=3):
     for j in range(n):
         t += rng.exponential(0.01)
         jobs.append(dict(L=int(rng.choice(sizes)), seed_J=700 + j, seed_spin=900 + j,
-                         beta=1.0 / float(rng.uniform(0.5, 1.5)), kind=("minstd", "mt19937")[j % 2],
+                         beta=1.0 / float(rng.uniform(0.5, 1.5)), kind=("minstd", "mt19937", "parisi_rapuano")[j % 3],
                          sweeps=int(rng.integers(5, 120)), arrival=t))
     return jobs
 
@@ -72,7 +72,8 @@ def test_served_jobs_equal_alone(isg, reference, budget, quantum, max_active):
 def test_served_jobs_match_oracle(isg):
     jobs = [dict(L=32, seed_J=5, seed_spin=6, beta=1 / 0.8, kind="mt19937", sweeps=40, arrival=0.0),
             dict(L=48, seed_J=7, seed_spin=8, beta=1 / 1.3, kind="minstd", sweeps=25, arrival=0.001),
-            dict(L=36, seed_J=9, seed_spin=10, beta=1 / 1.0, kind="mt19937", sweeps=33, arrival=0.002)]
+            dict(L=36, seed_J=9, seed_spin=10, beta=1 / 1.0, kind="mt19937", sweeps=33, arrival=0.002),
+            dict(L=40, seed_J=11, seed_spin=12, beta=1 / 0.9, kind="parisi_rapuano", sweeps=29, arrival=0.003)]
     srv = isg.Server(10**10, 10, 16)
     ids = [srv.submit(j["L"], j["seed_J"], j["seed_spin"], j["beta"], j["kind"], j["sweeps"], j["arrival"])
            for j in jobs]
