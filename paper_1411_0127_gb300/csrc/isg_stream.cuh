@@ -266,16 +266,18 @@ __device__ __forceinline__ bool level_lo(uint32_t d, const FlipArgs& a) {
 }
 
 // The two ballots of N consecutive 32-draw blocks.  A draw below cmp2 has
-// probability exp(-8 beta) (1.4e-4 at T = 0.9), so the warp first asks whether
-// any of its 32 N draws is below cmp2.  If none is, none is below cmp3 either,
-// every level is 0 or 1, and one comparison per draw gives it exactly.
-template <int N>
+// probability exp(-8 beta) (1.4e-4 at T = 0.9), so with TRIM the warp first asks
+// whether any of its 32 N draws is below cmp2.  If none is, none is below cmp3
+// either, every level is 0 or 1, and one comparison per draw gives it exactly.
+// The extra vote lengthens the dependency chain of a step, so kernels whose
+// warps are too few to hide latency are built without TRIM.
+template <int N, bool TRIM>
 __device__ __forceinline__ void level_ballots(const uint32_t (&d)[N], const FlipArgs& a, uint32_t (&lo)[N],
                                               uint32_t (&hi)[N]) {
     uint32_t dmin = d[0];
 #pragma unroll
     for (int j = 1; j < N; ++j) dmin = min(dmin, d[j]);
-    if (__any_sync(kFull, dmin < a.cmp2)) {
+    if (!TRIM || __any_sync(kFull, dmin < a.cmp2)) {
 #pragma unroll
         for (int j = 0; j < N; ++j) {
             lo[j] = __ballot_sync(kFull, level_lo(d[j], a));
@@ -291,8 +293,10 @@ __device__ __forceinline__ void level_ballots(const uint32_t (&d)[N], const Flip
 }
 
 // One pass of colour c over stream t; the stream state is in B / st.  SLACK is
-// the free space of the MT19937 window (see mt_window).
-template <typename Word, int KIND, int SLACK>
+// the free space of the MT19937 window (see mt_window); TRIM selects the
+// throughput form of the draw phase (level_ballots; MINSTD four blocks per step)
+// over the shorter-latency one (MINSTD two blocks per step).
+template <typename Word, int KIND, int SLACK, bool TRIM>
 __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t t, uint32_t* B, uint32_t* cond,
                                             StreamRegs& st, const StreamConst& k, int lane, int& dEsum) {
     constexpr int w = 8 * sizeof(Word);
@@ -309,30 +313,47 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t t,
         const int nrows = (int)((r_end - g0) < G ? (r_end - g0) : G);
         const int D = nrows * half;
         if (kMT) st.pos = (st.pos + D) % kMtN;  // the ring position after this group's draws
-        // draws in quads of four 32-draw blocks, then the remaining blocks one by one
-        const int nquads = D >> 7;
-        for (int q = 0; q < nquads; ++q) {
-            uint32_t d[4], lo[4], hi[4];
-            if (kMT) {
-                mt_quad<SLACK>(B, st.iA, d, k.mul, lane);
-            } else if (KIND == ISG_RNG_PARISI_RAPUANO) {
+        // draws four 32-draw blocks per step (MINSTD without TRIM: two), then the
+        // remaining blocks one by one
+        int b = 0;  // 32-draw blocks of this group done so far
+        if (KIND == ISG_RNG_MINSTD && !TRIM) {
+            const int npairs = D >> 6;
+            for (int q = 0; q < npairs; ++q) {
+                uint32_t d[2] = {st.xA, st.xB}, lo[2], hi[2];
+                st.xA = minstd_mulmod(st.xA, k.a64);
+                st.xB = minstd_mulmod(st.xB, k.a64);
+                level_ballots<2, false>(d, a, lo, hi);
+                if (lane == 0) {
+                    *(uint2*)(cond + 2 * q) = make_uint2(lo[0], lo[1]);
+                    *(uint2*)(cond + kCondWords + 2 * q) = make_uint2(hi[0], hi[1]);
+                }
+            }
+            b = 2 * npairs;
+        } else {
+            const int nquads = D >> 7;
+            for (int q = 0; q < nquads; ++q) {
+                uint32_t d[4], lo[4], hi[4];
+                if (kMT) {
+                    mt_quad<SLACK>(B, st.iA, d, k.mul, lane);
+                } else if (KIND == ISG_RNG_PARISI_RAPUANO) {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) d[j] = pr_warp_step(st.xA, st.xB, lane, 32);
-            } else {
-                d[0] = st.xA;
-                d[1] = st.xB;
-                d[2] = minstd_mulmod(st.xA, k.a64);
-                d[3] = minstd_mulmod(st.xB, k.a64);
-                st.xA = minstd_mulmod(d[2], k.a64);
-                st.xB = minstd_mulmod(d[3], k.a64);
+                    for (int j = 0; j < 4; ++j) d[j] = pr_warp_step(st.xA, st.xB, lane, 32);
+                } else {
+                    d[0] = st.xA;
+                    d[1] = st.xB;
+                    d[2] = minstd_mulmod(st.xA, k.a64);
+                    d[3] = minstd_mulmod(st.xB, k.a64);
+                    st.xA = minstd_mulmod(d[2], k.a64);
+                    st.xB = minstd_mulmod(d[3], k.a64);
+                }
+                level_ballots<4, TRIM>(d, a, lo, hi);
+                if (lane == 0) {
+                    *(uint4*)(cond + 4 * q) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                    *(uint4*)(cond + kCondWords + 4 * q) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                }
             }
-            level_ballots<4>(d, a, lo, hi);
-            if (lane == 0) {
-                *(uint4*)(cond + 4 * q) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-                *(uint4*)(cond + kCondWords + 4 * q) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-            }
+            b = 4 * nquads;
         }
-        int b = 4 * nquads;  // 32-draw blocks of this group done so far
         for (int rem = D - 32 * b; rem > 0; rem -= 32, ++b) {
             const int nvalid = rem < 32 ? rem : 32;
             uint32_t d;

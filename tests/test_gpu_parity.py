@@ -186,6 +186,22 @@ def test_large_workload_two_sweeps(isg):
     assert np.array_equal(g.read_spins(), o.spins())
 
 
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("L", [432, 512])
+def test_throughput_form_lattices(isg, L, kind):
+    """Lattices with at least 16 streams per SM (2456 and 4096 streams here) run
+    the throughput form of the draw phase (one comparison per draw when no draw
+    of a quad is below the second threshold); L = 432 has 32-bit words, L = 512
+    64-bit words.  Three sweeps at T = 1.1 against the oracle, all spins."""
+    g, o = pair(isg, L, kind, 1 / 1.1, seed_J=L + 1, seed_spin=L + 2)
+    assert g.info()["streams"] >= 2432
+    g.sweep(3)
+    o.sweep(3, threads=16)
+    assert g.tracked_energy() == o.tracked_energy()
+    assert g.hash() == o.hash()
+    assert np.array_equal(g.read_spins(), o.spins())
+
+
 # ------------------------------------------------------------- invariants ---
 
 @pytest.mark.parametrize("kind", KINDS)
