@@ -260,9 +260,18 @@ __device__ __forceinline__ void store_stream(const FlipArgs& a, int64_t t, const
     }
 }
 
+// The three compare values of a pass, held in registers: the batched engine
+// reads its FlipArgs from global memory, where the compiler could not keep them
+// across the shared-memory stores of the draw loop.
+struct Cmp {
+    uint32_t c1, c2, c3;
+};
+
+__device__ __forceinline__ Cmp cmp_of(const FlipArgs& a) { return Cmp{a.cmp1, a.cmp2, a.cmp3}; }
+
 // Level of a draw against the nested thresholds, as the two ballot bits.
-__device__ __forceinline__ bool level_lo(uint32_t d, const FlipArgs& a) {
-    return (d < a.cmp1) ^ (d < a.cmp2) ^ (d < a.cmp3);
+__device__ __forceinline__ bool level_lo(uint32_t d, const Cmp& a) {
+    return (d < a.c1) ^ (d < a.c2) ^ (d < a.c3);
 }
 
 // The two ballots of N consecutive 32-draw blocks.  A draw below cmp2 has
@@ -272,21 +281,21 @@ __device__ __forceinline__ bool level_lo(uint32_t d, const FlipArgs& a) {
 // The extra vote lengthens the dependency chain of a step, so kernels whose
 // warps are too few to hide latency are built without TRIM.
 template <int N, bool TRIM>
-__device__ __forceinline__ void level_ballots(const uint32_t (&d)[N], const FlipArgs& a, uint32_t (&lo)[N],
+__device__ __forceinline__ void level_ballots(const uint32_t (&d)[N], const Cmp& a, uint32_t (&lo)[N],
                                               uint32_t (&hi)[N]) {
     uint32_t dmin = d[0];
 #pragma unroll
     for (int j = 1; j < N; ++j) dmin = min(dmin, d[j]);
-    if (!TRIM || __any_sync(kFull, dmin < a.cmp2)) {
+    if (!TRIM || __any_sync(kFull, dmin < a.c2)) {
 #pragma unroll
         for (int j = 0; j < N; ++j) {
             lo[j] = __ballot_sync(kFull, level_lo(d[j], a));
-            hi[j] = __ballot_sync(kFull, d[j] < a.cmp2);
+            hi[j] = __ballot_sync(kFull, d[j] < a.c2);
         }
     } else {
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-            lo[j] = __ballot_sync(kFull, d[j] < a.cmp1);
+            lo[j] = __ballot_sync(kFull, d[j] < a.c1);
             hi[j] = 0u;
         }
     }
@@ -302,6 +311,7 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t t,
     constexpr int w = 8 * sizeof(Word);
     constexpr bool kMT = KIND == ISG_RNG_MT19937;
     const int W = a.W, half = a.half, L = a.L;
+    const Cmp cm = cmp_of(a);
     const int G = 32 / W;
     const int lj = lane / W, lk = lane - lj * W;
     const int loff = lj * half + lk * w;
@@ -322,7 +332,7 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t t,
                 uint32_t d[2] = {st.xA, st.xB}, lo[2], hi[2];
                 st.xA = minstd_mulmod(st.xA, k.a64);
                 st.xB = minstd_mulmod(st.xB, k.a64);
-                level_ballots<2, false>(d, a, lo, hi);
+                level_ballots<2, false>(d, cm, lo, hi);
                 if (lane == 0) {
                     *(uint2*)(cond + 2 * q) = make_uint2(lo[0], lo[1]);
                     *(uint2*)(cond + kCondWords + 2 * q) = make_uint2(hi[0], hi[1]);
@@ -346,7 +356,7 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t t,
                     st.xA = minstd_mulmod(d[2], k.a64);
                     st.xB = minstd_mulmod(d[3], k.a64);
                 }
-                level_ballots<4, TRIM>(d, a, lo, hi);
+                level_ballots<4, TRIM>(d, cm, lo, hi);
                 if (lane == 0) {
                     *(uint4*)(cond + 4 * q) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
                     *(uint4*)(cond + kCondWords + 4 * q) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
@@ -369,8 +379,8 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t t,
                 st.xA = src < 32 ? pa : pb;
                 st.xB = minstd_mulmod(st.xA, k.a32);
             }
-            const uint32_t lo = __ballot_sync(kFull, level_lo(d, a));
-            const uint32_t hi = __ballot_sync(kFull, d < a.cmp2);
+            const uint32_t lo = __ballot_sync(kFull, level_lo(d, cm));
+            const uint32_t hi = __ballot_sync(kFull, d < cm.c2);
             if (lane == 0) {
                 cond[b] = lo;
                 cond[kCondWords + b] = hi;
