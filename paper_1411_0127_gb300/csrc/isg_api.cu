@@ -77,8 +77,9 @@ static int alloc_sim(isg_sim* h) {
     const size_t rng_words = (size_t)h->S * rng_state_words(h->kind);
     h->rng = (uint32_t*)dev_alloc(h, rng_words * 4);
     h->rng_pos = (uint32_t*)dev_alloc(h, (size_t)h->S * 4);
+    if (h->kind == ISG_RNG_MINSTD) h->rng_alt = (uint32_t*)dev_alloc(h, rng_words * 4);
     h->scal = (long long*)dev_alloc(h, 8 * sizeof(long long));
-    if (!h->planes || !h->rng || !h->rng_pos || !h->scal) {
+    if (!h->planes || !h->rng || !h->rng_pos || !h->scal || (h->kind == ISG_RNG_MINSTD && !h->rng_alt)) {
         set_error("isg: device allocation failed (%zu bytes of planes)", pbytes);
         return ISG_ERR_NOMEM;
     }
@@ -94,6 +95,7 @@ static void free_sim(isg_sim* h) {
     dev_free(h, h->planes);
     dev_free(h, h->rng);
     dev_free(h, h->rng_pos);
+    dev_free(h, h->rng_alt);
     dev_free(h, h->scal);
     delete h;
 }
@@ -175,7 +177,7 @@ size_t sim_device_bytes(int L, int rng_kind, bool force32) {
     int64_t R = 0, S = 0;
     partition(L, &R, &S);
     const int64_t plane = (rows * W * (wbits / 8) + 255) / 256 * 256;
-    const int64_t rng = S * rng_state_words(rng_kind) * 4;
+    const int64_t rng = S * rng_state_words(rng_kind) * 4 * (rng_kind == ISG_RNG_MINSTD ? 2 : 1);
     return (size_t)(8 * plane + rng + S * 4 + 8 * (int64_t)sizeof(long long));
 }
 
@@ -435,7 +437,11 @@ int isg_load(const void* buf, size_t n, isg_sim** out) {
     h->seed_J = hd.seed_J;
     h->seed_spin = hd.seed_spin;
     h->seed_rng = hd.seed_rng;
-    h->force32 = hd.wbits == 32;
+    {
+        // 32-bit words where 64-bit ones would be chosen: the saved handle had them forced
+        const int half = h->L / 2, w64 = (half + 63) / 64, w32 = (half + 31) / 32;
+        h->force32 = hd.wbits == 32 && 2 * w64 == w32;
+    }
     thresholds(h->beta, h->thr);
     int rc = alloc_sim(h);
     if (rc) { free_sim(h); return rc; }

@@ -86,7 +86,8 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) batch_kernel(BatchArgs b,
                 const FlipArgs& a = b.reps[e.x];
                 if (!resident) load_stream<KIND>(a, e.y, ring, st, k, lane);
                 int dE = 0;
-                stream_pass<uint32_t, KIND, kBatchSlack, true>(a, pass & 1, e.y, ring, cond, st, k, lane, dE);
+                const int64_t rb = (int64_t)e.y * a.R, re = rb + a.R < a.rows ? rb + a.R : a.rows;
+                stream_pass<uint32_t, KIND, kBatchSlack, true>(a, pass & 1, rb, re, ring, cond, st, k, lane, dE);
                 if (!resident) store_stream<KIND>(a, e.y, ring, st, lane);
                 for (int sh = 16; sh; sh >>= 1) dE += __shfl_xor_sync(kFull, dE, sh);
                 if (lane == 0 && dE != 0) atomicAdd((unsigned long long*)a.dE, (unsigned long long)(long long)dE);

@@ -259,6 +259,7 @@ struct isg_sim {
     unsigned char* planes = nullptr;    // 8 planes: index 4*c + q, q = S, Jx, Jy, Jz
     uint32_t* rng = nullptr;            // MT: S * 624 ring words; MINSTD: S states
     uint32_t* rng_pos = nullptr;        // MT: S ring positions
+    uint32_t* rng_alt = nullptr;        // MINSTD: the other state buffer of segmented passes (see isg_flip_fast.cu)
     long long* scal = nullptr;          // [0] tracked dE, [1] scratch sum, [2] hash, [3] stream tickets
     unsigned long long tickets = 0;     // value of the stream-ticket counter before the next launch
     int64_t E0 = 0;                     // energy when tracking (re)started

@@ -6,6 +6,18 @@
 // grid fills the GPU once and every warp takes stream after stream from a
 // monotonically increasing ticket counter, so the last "wave" of streams is
 // spread over all SMs instead of leaving most of them idle.
+//
+// Segments (MINSTD, lattices with few streams): the draws of a stream are
+// x_j = x 16807^(j+1) mod (2^31 - 1), so a warp can start anywhere in the
+// stream by one multiplication.  When the lattice has too few streams to fill
+// the GPU, every stream is cut into nseg segments of whole row groups, each a
+// work item of its own, started from x 16807^(first draw index).  The stream's
+// end state x 16807^D is written by its last segment into the handle's other
+// state buffer (rng_alt), so no item can overwrite a state another item has
+// still to read; the host swaps the two buffers after the launch.
+#include <cstring>
+#include <utility>
+
 #include "isg_stream.cuh"
 
 namespace isg {
@@ -18,25 +30,55 @@ struct Tickets {
     unsigned long long base;      // its value when this launch starts
 };
 
+constexpr int kMaxSegments = 64;
+
+// Segmented launch (MINSTD only; nseg = 1 otherwise).
+struct Segments {
+    int nseg;                     // segments per stream
+    int64_t segrows;              // rows per segment, a multiple of the row-group height
+    uint32_t jump[kMaxSegments];  // 16807^(k segrows L/2) mod (2^31 - 1): start of segment k
+    uint32_t jend, jend_last;     // 16807^D for a full stream and for the last stream
+    uint32_t* rng_out;            // the other state buffer
+};
+
 template <typename Word, int KIND, bool TRIM>
 __global__ void __launch_bounds__(kFastWarps * 32, KIND == ISG_RNG_MT19937 ? 7 : 8)
-    flip_fast_kernel(FlipArgs a, StreamConst k, Tickets tk) {
+    flip_fast_kernel(FlipArgs a, StreamConst k, Tickets tk, Segments sg) {
     extern __shared__ uint32_t smem[];
     constexpr int kRing = KIND == ISG_RNG_MT19937 ? mt_window(kFastSlack) : 0;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint32_t* ring = smem + wid * (kRing + 2 * kCondWords);
     uint32_t* cond = ring + kRing;
+    const int64_t items = a.S * sg.nseg;
     int dEsum = 0;
     for (;;) {
         unsigned long long v = 0;
         if (lane == 0) v = atomicAdd(tk.counter, 1ull);
         v = __shfl_sync(kFull, v, 0);
-        const int64_t t = (int64_t)(v - tk.base);
-        if (t >= a.S) break;
+        const int64_t u = (int64_t)(v - tk.base);
+        if (u >= items) break;
         StreamRegs st;
-        load_stream<KIND>(a, t, ring, st, k, lane);
-        stream_pass<Word, KIND, kFastSlack, TRIM>(a, a.c, t, ring, cond, st, k, lane, dEsum);
-        store_stream<KIND>(a, t, ring, st, lane);
+        if (KIND == ISG_RNG_MINSTD && !TRIM && sg.nseg > 1) {  // segments: latency form only
+            const int64_t t = u / sg.nseg;
+            const int ks = (int)(u - t * sg.nseg);
+            const int64_t r0 = t * a.R, r1 = r0 + a.R < a.rows ? r0 + a.R : a.rows;
+            const int64_t rb = r0 + ks * sg.segrows;
+            const int64_t re = rb + sg.segrows < r1 ? rb + sg.segrows : r1;
+            const uint32_t x0 = a.rng[t];
+            if (rb < re) {
+                st.xA = minstd_mulmod(minstd_mulmod(x0, sg.jump[ks]), a.mt.pow[lane + 1]);
+                st.xB = minstd_mulmod(st.xA, k.a32);
+                stream_pass<Word, KIND, kFastSlack, TRIM>(a, a.c, rb, re, ring, cond, st, k, lane, dEsum);
+            }
+            if (ks == sg.nseg - 1 && lane == 0)
+                sg.rng_out[t] = minstd_mulmod(x0, t == a.S - 1 ? sg.jend_last : sg.jend);
+        } else {
+            const int64_t t = u;
+            load_stream<KIND>(a, t, ring, st, k, lane);
+            const int64_t rb = t * a.R, re = rb + a.R < a.rows ? rb + a.R : a.rows;
+            stream_pass<Word, KIND, kFastSlack, TRIM>(a, a.c, rb, re, ring, cond, st, k, lane, dEsum);
+            store_stream<KIND>(a, t, ring, st, lane);
+        }
     }
     for (int sh = 16; sh; sh >>= 1) dEsum += __shfl_xor_sync(kFull, dEsum, sh);
     if (lane == 0 && dEsum != 0) atomicAdd((unsigned long long*)a.dE, (unsigned long long)(long long)dEsum);
@@ -45,6 +87,44 @@ __global__ void __launch_bounds__(kFastWarps * 32, KIND == ISG_RNG_MT19937 ? 7 :
 // Streams per SM from which the throughput form of the draw phase (TRIM) is used:
 // below it too few warps are resident to hide the longer dependency chain.
 constexpr int64_t kTrimStreamsPerSM = 16;
+
+// a^e mod (2^31 - 1) by square and multiply (host).
+static uint32_t minstd_pow(uint32_t a, uint64_t e) {
+    uint32_t r = 1;
+    while (e) {
+        if (e & 1) r = minstd_mulmod(r, a);
+        a = minstd_mulmod(a, a);
+        e >>= 1;
+    }
+    return r;
+}
+
+// Segments of a MINSTD launch with fewer streams than the resident warps can
+// take (nseg = 1 otherwise): about two items per resident warp, each at least
+// one row group.  Not for batch members and batched server jobs (force32): their
+// state pointers are also held in device descriptors and captured graphs, which
+// the buffer swap would leave behind.
+static Segments plan_segments(const isg_sim* h, int64_t resident_warps, bool latency_form) {
+    Segments sg;
+    memset(&sg, 0, sizeof sg);
+    sg.nseg = 1;
+    if (h->kind != ISG_RNG_MINSTD || !latency_form || !h->rng_alt || h->force32) return sg;
+    const int64_t G = 32 / h->W;
+    const int64_t groups = (h->R + G - 1) / G;
+    int64_t nseg = (2 * resident_warps + h->S - 1) / h->S;
+    if (nseg > groups) nseg = groups;
+    if (nseg > kMaxSegments) nseg = kMaxSegments;
+    if (nseg < 2) return sg;
+    const int64_t gps = (groups + nseg - 1) / nseg;  // row groups per segment
+    sg.nseg = (int)((groups + gps - 1) / gps);
+    sg.segrows = gps * G;
+    for (int k = 0; k < sg.nseg; ++k) sg.jump[k] = minstd_pow(kMinstdA, (uint64_t)(k * sg.segrows * h->half));
+    const int64_t last_rows = h->rows - (h->S - 1) * h->R;
+    sg.jend = minstd_pow(kMinstdA, (uint64_t)(h->R * h->half));
+    sg.jend_last = minstd_pow(kMinstdA, (uint64_t)(last_rows * h->half));
+    sg.rng_out = h->rng_alt;
+    return sg;
+}
 
 template <typename Word, int KIND, bool TRIM>
 static cudaError_t launch_fast_t(isg_sim* h, int colour, cudaStream_t s, int sms) {
@@ -61,13 +141,17 @@ static cudaError_t launch_fast_t(isg_sim* h, int colour, cudaStream_t s, int sms
                                                                       kFastWarps * 32, smem);
         if (e != cudaSuccess || occ < 1) occ = 1;
     }
+    const Segments sg = plan_segments(h, (int64_t)sms * occ * kFastWarps, !TRIM);
+    const int64_t items = h->S * sg.nseg;
     int64_t blocks = (int64_t)sms * occ;
-    const int64_t need = (h->S + kFastWarps - 1) / kFastWarps;
+    const int64_t need = (items + kFastWarps - 1) / kFastWarps;
     if (blocks > need) blocks = need;
-    flip_fast_kernel<Word, KIND, TRIM><<<(unsigned)blocks, kFastWarps * 32, smem, s>>>(a, k, tk);
+    flip_fast_kernel<Word, KIND, TRIM><<<(unsigned)blocks, kFastWarps * 32, smem, s>>>(a, k, tk, sg);
     const cudaError_t e = cudaGetLastError();
-    // every warp takes one ticket past the last stream before it stops
-    if (e == cudaSuccess) h->tickets += (unsigned long long)h->S + (unsigned long long)blocks * kFastWarps;
+    if (e != cudaSuccess) return e;
+    // every warp takes one ticket past the last item before it stops
+    h->tickets += (unsigned long long)items + (unsigned long long)blocks * kFastWarps;
+    if (sg.nseg > 1) std::swap(h->rng, h->rng_alt);  // the end states are in the other buffer
     return e;
 }
 

@@ -301,13 +301,16 @@ __device__ __forceinline__ void level_ballots(const uint32_t (&d)[N], const Cmp&
     }
 }
 
-// One pass of colour c over stream t; the stream state is in B / st.  SLACK is
-// the free space of the MT19937 window (see mt_window); TRIM selects the
-// throughput form of the draw phase (level_ballots; MINSTD four blocks per step)
-// over the shorter-latency one (MINSTD two blocks per step).
+// One pass of colour c over rows [r_begin, r_end) of a stream (all of its rows,
+// or a segment that starts at a row group); the generator state, positioned at
+// the first of these rows, is in B / st.  SLACK is the free space of the
+// MT19937 window (see mt_window); TRIM selects the throughput form of the draw
+// phase (level_ballots; MINSTD four blocks per step) over the shorter-latency
+// one (MINSTD two blocks per step).
 template <typename Word, int KIND, int SLACK, bool TRIM>
-__device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t t, uint32_t* B, uint32_t* cond,
-                                            StreamRegs& st, const StreamConst& k, int lane, int& dEsum) {
+__device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t r_begin, int64_t r_end, uint32_t* B,
+                                            uint32_t* cond, StreamRegs& st, const StreamConst& k, int lane,
+                                            int& dEsum) {
     constexpr int w = 8 * sizeof(Word);
     constexpr bool kMT = KIND == ISG_RNG_MT19937;
     const int W = a.W, half = a.half, L = a.L;
@@ -315,8 +318,6 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t t,
     const int G = 32 / W;
     const int lj = lane / W, lk = lane - lj * W;
     const int loff = lj * half + lk * w;
-    const int64_t r_begin = t * a.R;
-    const int64_t r_end = r_begin + a.R < a.rows ? r_begin + a.R : a.rows;
     int r = (int)r_begin + lj;
     int y = r % L, z = r / L;
     for (int64_t g0 = r_begin; g0 < r_end; g0 += G) {
