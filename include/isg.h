@@ -134,6 +134,17 @@ int isg_read_spins(const isg_sim *h, int8_t *host_out, size_t n, void *cuda_stre
  * +1 or -1 gives ISG_ERR_ARG and changes nothing. */
 int isg_write_spins(isg_sim *h, const int8_t *host_in, size_t n, void *cuda_stream);
 
+/* Spins as packed bits in site order (sync): bit (i & 7) of byte i >> 3 of
+ * host_out is site i, 1 meaning s = +1 (Sec. 4 bit map).  nbytes must be at
+ * least ceil(L^3 / 8) (else ISG_ERR_ARG).  The compact form of isg_read_spins:
+ * one eighth of the bytes to move. */
+int isg_read_spins_packed(const isg_sim *h, uint8_t *host_out, size_t nbytes, void *cuda_stream);
+
+/* Overwrite the spins from packed bits in the format of isg_read_spins_packed
+ * (sync; every bit pattern is a valid configuration); the tracked energy
+ * restarts.  nbytes >= ceil(L^3 / 8) (else ISG_ERR_ARG and nothing changes). */
+int isg_write_spins_packed(isg_sim *h, const uint8_t *host_in, size_t nbytes, void *cuda_stream);
+
 /* Copy the couplings to host_out as int8 +-1, [d][i] (sync); n >= 3 L^3. */
 int isg_read_couplings(const isg_sim *h, int8_t *host_out, size_t n, void *cuda_stream);
 

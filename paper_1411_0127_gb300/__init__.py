@@ -44,6 +44,8 @@ SIGNATURES = {
     "isg_hash": (_i32, [_vp, _vp, _vp]),
     "isg_read_spins": (_i32, [_vp, _vp, _sz, _vp]),
     "isg_write_spins": (_i32, [_vp, _vp, _sz, _vp]),
+    "isg_read_spins_packed": (_i32, [_vp, _vp, _sz, _vp]),
+    "isg_write_spins_packed": (_i32, [_vp, _vp, _sz, _vp]),
     "isg_read_couplings": (_i32, [_vp, _vp, _sz, _vp]),
     "isg_write_couplings": (_i32, [_vp, _vp, _sz, _vp]),
     "isg_save": (_i32, [_vp, _vp, _vp, _vp]),
@@ -235,10 +237,30 @@ class Sim:
         _check(lib().isg_hash(self._h, ctypes.byref(v), _stream(stream)))
         return v.value
 
-    def read_spins(self, stream=None) -> np.ndarray:
-        out = np.empty(self.N, dtype=np.int8)
+    def read_spins(self, stream=None, out: np.ndarray = None) -> np.ndarray:
+        """Spins as int8 +-1 in site order.  `out` (C-contiguous int8, at least
+        L^3 values; pinned memory for full copy speed) receives them directly."""
+        if out is None:
+            out = np.empty(self.N, dtype=np.int8)
+        elif out.dtype != np.int8 or not out.flags["C_CONTIGUOUS"] or out.size < self.N:
+            raise ValueError("out must be a C-contiguous int8 array of at least L^3 values")
         _check(lib().isg_read_spins(self._h, _ptr(out), out.size, _stream(stream)))
         return out
+
+    def read_spins_packed(self, stream=None, out: np.ndarray = None) -> np.ndarray:
+        """Spins as packed bits (uint8, ceil(L^3/8) bytes): bit i & 7 of byte i >> 3
+        is site i, 1 meaning +1 (numpy.unpackbits(..., bitorder="little"))."""
+        nb = (self.N + 7) // 8
+        if out is None:
+            out = np.empty(nb, dtype=np.uint8)
+        elif out.dtype != np.uint8 or not out.flags["C_CONTIGUOUS"] or out.size < nb:
+            raise ValueError("out must be a C-contiguous uint8 array of at least ceil(L^3/8) bytes")
+        _check(lib().isg_read_spins_packed(self._h, _ptr(out), out.size, _stream(stream)))
+        return out
+
+    def write_spins_packed(self, bits: np.ndarray, stream=None):
+        bits = np.ascontiguousarray(bits, dtype=np.uint8).reshape(-1)
+        _check(lib().isg_write_spins_packed(self._h, _ptr(bits), bits.size, _stream(stream)))
 
     def write_spins(self, s: np.ndarray, stream=None):
         s = np.ascontiguousarray(s, dtype=np.int8).reshape(-1)

@@ -312,14 +312,46 @@ static int read_int8(const isg_sim* hc, int8_t* out, size_t n, size_t need, cuda
     if (n < need) { set_error("read: buffer holds %zu values, %zu needed", n, need); return ISG_ERR_ARG; }
     int8_t* d = (int8_t*)dev_alloc(h, need);
     if (!d) { set_error("read: device allocation failed"); return ISG_ERR_NOMEM; }
-    cudaError_t e = couplings ? launch_unpack_couplings(h, d, s) : launch_unpack_spins(h, d, s);
+    cudaError_t e = couplings ? launch_unpack_couplings(h, d, s) : launch_unpack_spins_fast(h, d, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, need, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     dev_free(h, d);
     return e == cudaSuccess ? ISG_OK : cuda_fail(e, "read");
 }
 
+// Spins from int8 +-1: validated and packed in one pass into a scratch copy of
+// the two spin planes, which replaces them only if every value was +1 or -1.
+static int write_spins_int8(isg_sim* h, const int8_t* in, size_t n, size_t need, cudaStream_t s) {
+    if (n < need) { set_error("write: buffer holds %zu values, %zu needed", n, need); return ISG_ERR_ARG; }
+    int8_t* d = (int8_t*)dev_alloc(h, need);
+    unsigned char* scratch = (unsigned char*)dev_alloc(h, 2 * (size_t)h->plane_bytes);
+    int* bad = (int*)dev_alloc(h, sizeof(int));
+    if (!d || !scratch || !bad) {
+        dev_free(h, d);
+        dev_free(h, scratch);
+        dev_free(h, bad);
+        set_error("write: device allocation failed");
+        return ISG_ERR_NOMEM;
+    }
+    int hbad = 0;
+    cudaError_t e = cudaMemcpyAsync(d, in, need, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = launch_pack_spins_checked(h, d, scratch, bad, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (int c = 0; c < 2 && e == cudaSuccess && !hbad; ++c)
+        e = cudaMemcpyAsync(h->plane(c, 0), scratch + (size_t)c * h->plane_bytes, (size_t)h->plane_bytes,
+                            cudaMemcpyDeviceToDevice, s);
+    dev_free(h, d);
+    dev_free(h, scratch);
+    dev_free(h, bad);
+    if (e != cudaSuccess) return cuda_fail(e, "write");
+    if (hbad) { set_error("write: values must be +1 or -1"); return ISG_ERR_ARG; }
+    return restart_tracking(h, s);
+}
+
 static int write_int8(isg_sim* h, const int8_t* in, size_t n, size_t need, cudaStream_t s, bool couplings) {
+    if (!couplings) return write_spins_int8(h, in, n, need, s);
     if (n < need) { set_error("write: buffer holds %zu values, %zu needed", n, need); return ISG_ERR_ARG; }
     int8_t* d = (int8_t*)dev_alloc(h, need);
     int* bad = (int*)dev_alloc(h, sizeof(int));
@@ -336,7 +368,7 @@ static int write_int8(isg_sim* h, const int8_t* in, size_t n, size_t need, cudaS
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess && !hbad) {
-        e = couplings ? launch_pack_couplings(h, d, s) : launch_pack_spins(h, d, s);
+        e = launch_pack_couplings(h, d, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     }
     dev_free(h, d);
@@ -354,6 +386,38 @@ int isg_read_spins(const isg_sim* h, int8_t* out, size_t n, void* stream) {
 int isg_write_spins(isg_sim* h, const int8_t* in, size_t n, void* stream) {
     if (!h || !in) { set_error("isg_write_spins: NULL argument"); return ISG_ERR_ARG; }
     return write_int8(h, in, n, (size_t)h->L * h->L * h->L, (cudaStream_t)stream, false);
+}
+
+int isg_read_spins_packed(const isg_sim* hc, uint8_t* out, size_t nbytes, void* stream) {
+    if (!hc || !out) { set_error("isg_read_spins_packed: NULL argument"); return ISG_ERR_ARG; }
+    isg_sim* h = const_cast<isg_sim*>(hc);
+    const int64_t N = (int64_t)h->L * h->L * h->L;
+    const size_t need = (size_t)((N + 7) / 8);
+    if (nbytes < need) { set_error("isg_read_spins_packed: buffer holds %zu bytes, %zu needed", nbytes, need); return ISG_ERR_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t* d = (uint32_t*)dev_alloc(h, (size_t)((N + 31) / 32) * 4);
+    if (!d) { set_error("isg_read_spins_packed: device allocation failed"); return ISG_ERR_NOMEM; }
+    cudaError_t e = launch_unpack_spins_bits(h, d, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, need, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dev_free(h, d);
+    return e == cudaSuccess ? ISG_OK : cuda_fail(e, "isg_read_spins_packed");
+}
+
+int isg_write_spins_packed(isg_sim* h, const uint8_t* in, size_t nbytes, void* stream) {
+    if (!h || !in) { set_error("isg_write_spins_packed: NULL argument"); return ISG_ERR_ARG; }
+    const int64_t N = (int64_t)h->L * h->L * h->L;
+    const size_t need = (size_t)((N + 7) / 8);
+    if (nbytes < need) { set_error("isg_write_spins_packed: buffer holds %zu bytes, %zu needed", nbytes, need); return ISG_ERR_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t* d = (uint32_t*)dev_alloc(h, (size_t)((N + 31) / 32) * 4);
+    if (!d) { set_error("isg_write_spins_packed: device allocation failed"); return ISG_ERR_NOMEM; }
+    cudaError_t e = cudaMemcpyAsync(d, in, need, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_pack_spins_bits(h, d, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dev_free(h, d);
+    if (e != cudaSuccess) return cuda_fail(e, "isg_write_spins_packed");
+    return restart_tracking(h, s);
 }
 
 int isg_read_couplings(const isg_sim* h, int8_t* out, size_t n, void* stream) {

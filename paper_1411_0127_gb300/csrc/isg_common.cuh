@@ -294,8 +294,12 @@ cudaError_t launch_flip_fast(isg_sim* h, int colour, cudaStream_t s);
 cudaError_t launch_energy(const isg_sim* h, long long* out, cudaStream_t s);
 cudaError_t launch_overlap(const isg_sim* a, const isg_sim* b, long long* out, cudaStream_t s);
 cudaError_t launch_hash(const isg_sim* h, unsigned long long* out, cudaStream_t s);
-cudaError_t launch_unpack_spins(const isg_sim* h, int8_t* dev_out, cudaStream_t s);
-cudaError_t launch_pack_spins(isg_sim* h, const int8_t* dev_in, cudaStream_t s);
+// spin I/O (isg_spinio.cu): int8 +-1 and packed bits in site order
+cudaError_t launch_unpack_spins_fast(const isg_sim* h, int8_t* dev_out, cudaStream_t s);
+cudaError_t launch_pack_spins_checked(const isg_sim* h, const int8_t* dev_in, unsigned char* dev_scratch, int* dev_bad,
+                                      cudaStream_t s);
+cudaError_t launch_unpack_spins_bits(const isg_sim* h, uint32_t* dev_out, cudaStream_t s);
+cudaError_t launch_pack_spins_bits(isg_sim* h, const uint32_t* dev_in, cudaStream_t s);
 cudaError_t launch_unpack_couplings(const isg_sim* h, int8_t* dev_out, cudaStream_t s);
 cudaError_t launch_pack_couplings(isg_sim* h, const int8_t* dev_in, cudaStream_t s);
 cudaError_t launch_check_pm1(const int8_t* dev_in, int64_t n, int* dev_bad, cudaStream_t s);

@@ -1,6 +1,7 @@
 // isg_measure.cu -- popcount kernels for the energy (Eq. 1), the replica
-// overlap and the Zobrist hash, and the kernels that convert between the bit
-// planes and int8 +-1 arrays in site order i = x + L*y + L*L*z.
+// overlap and the Zobrist hash, and the kernels that convert the coupling planes
+// to and from int8 +-1 arrays in site order i = x + L*y + L*L*z (the spins'
+// conversions are in isg_spinio.cu).
 //
 // Energy: every coupling is the forward (+x, +y or +z) coupling of exactly one
 // site, so U = number of unsatisfied bonds = sum over both colours and all words
@@ -185,22 +186,6 @@ __global__ void pack_kernel(MeasGeom g, int q, const int8_t* in) {
         }
         ((Word*)(g.planes + (size_t)(4 * c + q) * g.plane_bytes))[(size_t)r * g.W + k] = word;
     }
-}
-
-cudaError_t launch_unpack_spins(const isg_sim* h, int8_t* out, cudaStream_t s) {
-    const MeasGeom g = mgeom(h);
-    const int64_t N = (int64_t)h->L * h->L * h->L;
-    if (h->wbits == 64) unpack_kernel<uint64_t><<<grid_for(N, 256), 256, 0, s>>>(g, 0, out);
-    else unpack_kernel<uint32_t><<<grid_for(N, 256), 256, 0, s>>>(g, 0, out);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_pack_spins(isg_sim* h, const int8_t* in, cudaStream_t s) {
-    const MeasGeom g = mgeom(h);
-    const int64_t nw = 2 * h->rows * h->W;
-    if (h->wbits == 64) pack_kernel<uint64_t><<<grid_for(nw, 256), 256, 0, s>>>(g, 0, in);
-    else pack_kernel<uint32_t><<<grid_for(nw, 256), 256, 0, s>>>(g, 0, in);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_unpack_couplings(const isg_sim* h, int8_t* out, cudaStream_t s) {

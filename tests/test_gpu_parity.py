@@ -224,6 +224,44 @@ def test_segmented_minstd_streams(isg, L):
     assert g.hash() == c.hash() == o.hash()
 
 
+@pytest.mark.parametrize("L", [4, 10, 34, 64, 128, 130, 256])
+def test_spin_io_formats(isg, L):
+    """int8 and packed-bit spin I/O against the oracle: L = 64, 128 and 256 take
+    the vector path of the int8 packer (L a multiple of twice the word width),
+    the others the scalar path, with rows that start inside words and tails
+    shorter than 16 or 32 sites."""
+    g, o = pair(isg, L, "mt19937", 1 / 0.9, seed_J=L, seed_spin=L + 1)
+    g.sweep(3)
+    o.sweep(3)
+    ref = o.spins()
+    np.testing.assert_array_equal(g.read_spins(), ref)
+    bits = g.read_spins_packed()
+    np.testing.assert_array_equal(bits, np.packbits(ref == 1, bitorder="little"))
+    # round trips through both formats, with another configuration
+    rng = np.random.default_rng(L)
+    s = np.where(rng.random(L**3) < 0.5, 1, -1).astype(np.int8)
+    g.write_spins(s)
+    np.testing.assert_array_equal(g.read_spins(), s)
+    assert g.tracked_energy() == g.energy()
+    s2 = -s
+    g.write_spins_packed(np.packbits(s2 == 1, bitorder="little"))
+    np.testing.assert_array_equal(g.read_spins(), s2)
+    np.testing.assert_array_equal(g.read_spins_packed(), np.packbits(s2 == 1, bitorder="little"))
+    assert g.tracked_energy() == g.energy()
+    o.set_spins(s2)
+    assert g.energy() == o.energy()
+    # a rejected int8 array changes nothing
+    bad = s.copy()
+    bad[L**3 // 2] = 0
+    with pytest.raises(isg.IsgError):
+        g.write_spins(bad)
+    np.testing.assert_array_equal(g.read_spins(), s2)
+    # reading into a caller's buffer
+    buf = np.zeros(L**3 + 5, dtype=np.int8)
+    assert g.read_spins(out=buf) is buf
+    np.testing.assert_array_equal(buf[:L**3], s2)
+
+
 # ------------------------------------------------------------- invariants ---
 
 @pytest.mark.parametrize("kind", KINDS)
