@@ -41,8 +41,10 @@ struct Segments {
     uint32_t* rng_out;            // the other state buffer
 };
 
+// The throughput form keeps 7 (MT19937: shared memory) or 8 blocks of 4 warps
+// per SM; the latency form runs with few warps and may use more registers.
 template <typename Word, int KIND, bool TRIM>
-__global__ void __launch_bounds__(kFastWarps * 32, KIND == ISG_RNG_MT19937 ? 7 : 8)
+__global__ void __launch_bounds__(kFastWarps * 32, TRIM ? (KIND == ISG_RNG_MT19937 ? 7 : 8) : 2)
     flip_fast_kernel(FlipArgs a, StreamConst k, Tickets tk, Segments sg) {
     extern __shared__ uint32_t smem[];
     constexpr int kRing = KIND == ISG_RNG_MT19937 ? mt_window(kFastSlack) : 0;
@@ -145,7 +147,7 @@ static cudaError_t launch_fast_t(isg_sim* h, int colour, cudaStream_t s, int sms
     const int64_t items = h->S * sg.nseg;
     int64_t blocks = (int64_t)sms * occ;
     const int64_t need = (items + kFastWarps - 1) / kFastWarps;
-    if (blocks > need) blocks = need;
+    if (blocks > need) blocks = need > sms ? need : (sms < blocks ? sms : blocks);  // at least one block per SM
     flip_fast_kernel<Word, KIND, TRIM><<<(unsigned)blocks, kFastWarps * 32, smem, s>>>(a, k, tk, sg);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -145,6 +145,34 @@ __device__ __forceinline__ void mt_quad(uint32_t* B, int& iA, uint32_t d[4], con
     for (int j = 0; j < 4; ++j) d[j] = mt_temper_mul(d[j], k);
 }
 
+// Seven 32-draw blocks (224 draws) at once, for warps too few to hide latency:
+// block j reads x_{k+32j+l+397} with 32j + l + 397 <= 620 < 624, i.e. words that
+// exist before the step, so the reads again all precede the writes.  227 draws is
+// the most one step of the recurrence allows.
+template <int SLACK>
+__device__ __forceinline__ void mt_seven(uint32_t* B, int& iA, uint32_t d[7], const MtMul& k, int lane) {
+    mt_make_room<SLACK>(B, iA, 224, lane);
+    uint32_t a[7], b[7], m[7];
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+        const int i = iA + 32 * j + lane;
+        a[j] = B[i];
+        b[j] = B[i + 1];
+        m[j] = B[i + kMtM];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+        const uint32_t v = mt_twist(a[j], b[j], m[j], k);
+        B[iA + 32 * j + lane + kMtN] = v;
+        d[j] = v;
+    }
+    __syncwarp();
+    iA += 224;
+#pragma unroll
+    for (int j = 0; j < 7; ++j) d[j] = mt_temper_mul(d[j], k);
+}
+
 // One block of up to 32 draws (tail of a row group); lanes >= nvalid consume nothing.
 template <int SLACK>
 __device__ __forceinline__ uint32_t mt_single(uint32_t* B, int& iA, int lane, int nvalid, const MtMul& k) {
@@ -160,14 +188,24 @@ __device__ __forceinline__ uint32_t mt_single(uint32_t* B, int& iA, int lane, in
 }
 
 // Logic phase for one word of colour c at row r = y + L z, word k (see the
-// layout notes in isg_common.cuh); adds the word's dE to dEsum.
+// layout notes in isg_common.cuh), in two halves: word_load issues the loads of
+// the word, its forward couplings and the other colour's neighbour words (and
+// of the backward couplings there); word_compute counts the unsatisfied bonds,
+// forms the flip mask from the draws' bit streams, writes the word and adds its
+// dE to dEsum.  Between the two a warp can make the group's draws, so that the
+// loads' latency is hidden behind generator work.
 template <typename Word>
-__device__ __forceinline__ void word_update(const FlipArgs& a, int c, int r, int y, int z, int k,
-                                            const uint32_t* cond, int off, int& dEsum) {
-    constexpr int w = 8 * sizeof(Word);
-    const int L = a.L, W = a.W, nt = a.nt;
+struct WordIn {
+    size_t o;
+    int p;
+    Word s, na, jxc, jyc, jzc, syp, jym, sym, szp, jzm, szm, jxn, jxb, sb;
+};
+
+template <typename Word>
+__device__ __forceinline__ void word_load(const FlipArgs& a, int c, int r, int y, int z, int k, WordIn<Word>& q) {
+    const int L = a.L, W = a.W;
     const size_t pb = (size_t)a.plane_bytes;
-    Word* Sc = (Word*)(a.planes + (size_t)(4 * c) * pb);
+    const Word* Sc = (const Word*)(a.planes + (size_t)(4 * c) * pb);
     const Word* Jxc = (const Word*)(a.planes + (size_t)(4 * c + 1) * pb);
     const Word* Jyc = (const Word*)(a.planes + (size_t)(4 * c + 2) * pb);
     const Word* Jzc = (const Word*)(a.planes + (size_t)(4 * c + 3) * pb);
@@ -177,28 +215,49 @@ __device__ __forceinline__ void word_update(const FlipArgs& a, int c, int r, int
     const Word* Jyn = (const Word*)(a.planes + (size_t)(4 * n + 2) * pb);
     const Word* Jzn = (const Word*)(a.planes + (size_t)(4 * n + 3) * pb);
 
-    const int p = (c + y + z) & 1;
+    q.p = (c + y + z) & 1;
     const int rowW = r * W;
     const int dym = (y == 0 ? L - 1 : -1) * W, dyp = (y == L - 1 ? 1 - L : 1) * W;
     const int LW = L * W;
     const int dzm = (z == 0 ? (L - 1) * LW : -LW), dzp = (z == L - 1 ? -(L - 1) * LW : LW);
-    const size_t o = (size_t)(rowW + k);
+    q.o = (size_t)(rowW + k);
+    // the x neighbour word across the word boundary: k - 1 for p = 0, k + 1 for p = 1
+    const size_t onb = (size_t)(rowW + (q.p == 0 ? (k == 0 ? W - 1 : k - 1) : (k == W - 1 ? 0 : k + 1)));
+    const size_t o = q.o;
+    q.s = Sc[o];
+    q.na = Sn[o];
+    q.jxc = Jxc[o];
+    q.jyc = Jyc[o];
+    q.jzc = Jzc[o];
+    q.syp = Sn[o + dyp];
+    q.jym = Jyn[o + dym];
+    q.sym = Sn[o + dym];
+    q.szp = Sn[o + dzp];
+    q.jzm = Jzn[o + dzm];
+    q.szm = Sn[o + dzm];
+    q.jxn = Jxn[o];
+    q.jxb = q.p == 0 ? Jxn[onb] : Word(0);
+    q.sb = Sn[onb];
+}
 
-    const Word s = Sc[o];
-    const Word na = Sn[o];
-    const Word e_yp = Jyc[o] ^ s ^ Sn[o + dyp];
-    const Word e_ym = Jyn[o + dym] ^ s ^ Sn[o + dym];
-    const Word e_zp = Jzc[o] ^ s ^ Sn[o + dzp];
-    const Word e_zm = Jzn[o + dzm] ^ s ^ Sn[o + dzm];
+template <typename Word>
+__device__ __forceinline__ void word_compute(const FlipArgs& a, int c, const WordIn<Word>& q, int k,
+                                             const uint32_t* cond, int off, int& dEsum) {
+    constexpr int w = 8 * sizeof(Word);
+    const int W = a.W, nt = a.nt;
+    Word* Sc = (Word*)(a.planes + (size_t)(4 * c) * (size_t)a.plane_bytes);
+    const Word s = q.s, na = q.na;
+    const Word e_yp = q.jyc ^ s ^ q.syp;
+    const Word e_ym = q.jym ^ s ^ q.sym;
+    const Word e_zp = q.jzc ^ s ^ q.szp;
+    const Word e_zm = q.jzm ^ s ^ q.szm;
     Word e_xp, e_xm;
-    if (p == 0) {
-        const size_t onb = (size_t)(rowW + (k == 0 ? W - 1 : k - 1));
-        e_xp = Jxc[o] ^ s ^ na;
-        e_xm = row_down<Word>(Jxn[o] ^ na, Jxn[onb] ^ Sn[onb], k, nt) ^ s;
+    if (q.p == 0) {
+        e_xp = q.jxc ^ s ^ na;
+        e_xm = row_down<Word>(q.jxn ^ na, q.jxb ^ q.sb, k, nt) ^ s;
     } else {
-        const size_t onb = (size_t)(rowW + (k == W - 1 ? 0 : k + 1));
-        e_xp = Jxc[o] ^ s ^ row_up<Word>(na, Sn[onb], k, W, nt);
-        e_xm = Jxn[o] ^ s ^ na;
+        e_xp = q.jxc ^ s ^ row_up<Word>(na, q.sb, k, W, nt);
+        e_xm = q.jxn ^ s ^ na;
     }
     Word u0, u1, u2;
     Logic<Word>::count6(e_xp, e_xm, e_yp, e_ym, e_zp, e_zm, u0, u1, u2);
@@ -206,8 +265,16 @@ __device__ __forceinline__ void word_update(const FlipArgs& a, int c, int r, int
     const Word hi = take_bits<Word>(cond + kCondWords, off);
     Word f = Logic<Word>::flip(u0, u1, u2, lo | hi, hi, lo & hi);
     if (k == W - 1 && nt < w) f &= (Word)((Word(1) << nt) - 1);
-    Sc[o] = s ^ f;
+    Sc[q.o] = s ^ f;
     dEsum += Logic<Word>::dE(f, u0, u1, u2);
+}
+
+template <typename Word>
+__device__ __forceinline__ void word_update(const FlipArgs& a, int c, int r, int y, int z, int k,
+                                            const uint32_t* cond, int off, int& dEsum) {
+    WordIn<Word> q;
+    word_load<Word>(a, c, r, y, z, k, q);
+    word_compute<Word>(a, c, q, k, cond, off, dEsum);
 }
 
 // Generator state of the stream a warp is working on.
@@ -324,10 +391,33 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t r_
         const int nrows = (int)((r_end - g0) < G ? (r_end - g0) : G);
         const int D = nrows * half;
         if (kMT) st.pos = (st.pos + D) % kMtN;  // the ring position after this group's draws
+        // latency form: the group's plane words are loaded before its draws are made
+        WordIn<Word> win;
+        const bool act = lane < nrows * W;
+        if (!TRIM && act) word_load<Word>(a, c, r, y, z, lk, win);
         // draws four 32-draw blocks per step (MINSTD without TRIM: two), then the
         // remaining blocks one by one
         int b = 0;  // 32-draw blocks of this group done so far
-        if (KIND == ISG_RNG_MINSTD && !TRIM) {
+        if (kMT && !TRIM) {
+            const int nsev = D / 224;
+            for (int q = 0; q < nsev; ++q) {
+                uint32_t d[7], lo[7], hi[7];
+                mt_seven<SLACK>(B, st.iA, d, k.mul, lane);
+                level_ballots<7, false>(d, cm, lo, hi);
+                uint32_t l = lo[0], h = hi[0];
+#pragma unroll
+                for (int j = 1; j < 7; ++j)
+                    if (lane == j) {
+                        l = lo[j];
+                        h = hi[j];
+                    }
+                if (lane < 7) {
+                    cond[7 * q + lane] = l;
+                    cond[kCondWords + 7 * q + lane] = h;
+                }
+            }
+            b = 7 * nsev;
+        } else if (KIND == ISG_RNG_MINSTD && !TRIM) {
             const int npairs = D >> 6;
             for (int q = 0; q < npairs; ++q) {
                 uint32_t d[2] = {st.xA, st.xB}, lo[2], hi[2];
@@ -388,7 +478,10 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t r_
             }
         }
         __syncwarp();
-        if (lane < nrows * W) word_update<Word>(a, c, r, y, z, lk, cond, loff, dEsum);
+        if (act) {
+            if (TRIM) word_update<Word>(a, c, r, y, z, lk, cond, loff, dEsum);
+            else word_compute<Word>(a, c, win, lk, cond, loff, dEsum);
+        }
         __syncwarp();
         r += G;
         y += G;
