@@ -227,6 +227,7 @@ def batched_section(a, stream) -> dict:
     b = isg.Batch([x.L for x in samples], [x.seed_J for x in samples],
                   [v for x in samples for v in x.seed_spin], [1.0 / x.T for x in samples], "mt19937")
     attempts = b.info()["attempts_per_sweep"]
+    tuned = b.autotune(sweeps=8, stream=stream)       # untimed: candidates timed on a twin batch
     group = 64
     b.run(group, group, stream)                      # warm-up (captures the graph)
     torch.cuda.synchronize()
@@ -241,7 +242,11 @@ def batched_section(a, stream) -> dict:
                        "MT19937, sampler seed 7; %d attempts per sweep" % attempts,
            "group_sweeps": group, "timed_sweeps": sweeps, "launches": a.batch_groups,
            "psflip": ms * 1e9 / (sweeps * attempts),
-           "samples_sweeps_per_s": len(samples) * sweeps / (ms / 1e3)}
+           "samples_sweeps_per_s": len(samples) * sweeps / (ms / 1e3),
+           "autotune": {"config": list(tuned["config"]), "candidates": len(tuned["table"]),
+                        "psflip_by_config_8_sweeps": {"%d/%d/%d" % tuple(c): round(p, 4) for c, p in tuned["table"]},
+                        "note": "config = CTA shape (0: 32x1, 1: 24x1, 2: 16x1, 3: 16x2 warps x CTAs per SM) / "
+                                "streams per bundle / resident generator state"}}
     members = [b.member(r) for r in range(2 * len(samples))]
     for name, fn in (("plain_one_sample_per_launch_psflip", "sweep_plain"),
                      ("fast_one_sample_per_launch_psflip", "sweep")):

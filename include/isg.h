@@ -184,6 +184,26 @@ void isg_batch_destroy(isg_batch *b);
  * bundle) and of spin-flip attempts per sweep of the whole batch. */
 int isg_batch_info(const isg_batch *b, int *samples, int *bundles, int64_t *attempts_per_sweep);
 
+/* Execution configuration of the batch's persistent launches, the space the
+ * autotuner (paper_1411_0127_gb300/autotune.py) searches.  No configuration
+ * changes a result: every replica follows its own trajectory whatever the
+ * bundles, so all of them give bit-identical states.
+ *   shape     CTA shape: 0 = one CTA of 32 warps per SM, 1 = one of 24,
+ *             2 = one of 16, 3 = two of 16 (the "tile": warps sweeping a bundle)
+ *   capacity  streams per packed bundle of small lattices, 1 .. warps of the
+ *             shape; 0 = the shape's warps
+ *   resident  1: the generator state of a bundle that fits in the CTA stays in
+ *             shared memory / registers for a whole launch; 0: it is loaded and
+ *             stored around every colour pass
+ * Words per thread are fixed: one 32-bit word of a row group per lane.
+ * Synchronises the device, re-plans the bundles and drops the captured graph;
+ * ISG_ERR_ARG for an unknown shape, a capacity above the shape's warps or a
+ * resident flag other than 0/1.  The default is (0, 32, 1). */
+int isg_batch_set_config(isg_batch *b, int shape, int capacity, int resident);
+
+/* The current configuration (any pointer may be NULL). */
+int isg_batch_get_config(const isg_batch *b, int *shape, int *capacity, int *resident);
+
 /* Handle of replica i (0 <= i < 2n; replicas 2s, 2s+1 belong to sample s).  The
  * handle stays owned by the batch: use it with the measuring, reading and
  * checkpoint calls, never with isg_destroy. */

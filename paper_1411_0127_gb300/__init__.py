@@ -57,6 +57,8 @@ SIGNATURES = {
     "isg_batch_destroy": (None, [_vp]),
     "isg_batch_info": (_i32, [_vp, _vp, _vp, _vp]),
     "isg_batch_member": (_i32, [_vp, _i32, _PP]),
+    "isg_batch_set_config": (_i32, [_vp, _i32, _i32, _i32]),
+    "isg_batch_get_config": (_i32, [_vp, _vp, _vp, _vp]),
     "isg_batch_run": (_i32, [_vp, _i64, _i32, _vp]),
     "isg_batch_measure": (_i32, [_vp, _vp, _vp, _vp]),
     "isg_batch_tracked": (_i32, [_vp, _vp, _vp, _vp]),
@@ -337,6 +339,30 @@ class Batch:
         self.n, self.kind = n, kind
         self.L = [int(v) for v in La]
         self.beta = [float(v) for v in B]
+        self._args = (list(self.L), [int(v) for v in J], [int(v) for v in S], list(self.beta), kind)
+
+    def set_config(self, shape: int, capacity: int = 0, resident: int = 1):
+        """Execution configuration (see isg_batch_set_config); results do not depend on it."""
+        _check(lib().isg_batch_set_config(self._h, int(shape), int(capacity), int(resident)))
+
+    def get_config(self) -> tuple:
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().isg_batch_get_config(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    def twin(self) -> "Batch":
+        """A new batch with the same samples, seeds, temperatures and kind, at
+        sweep 0 (the autotuner times candidates on one)."""
+        L, J, S, B, kind = self._args
+        return Batch(L, J, S, B, kind)
+
+    def autotune(self, sweeps: int = 8, cache: str = None, stream=None) -> dict:
+        """Choose the fastest execution configuration (paper_1411_0127_gb300.autotune)
+        and apply it; the batch's own state is not touched."""
+        from . import autotune as _at
+        res = _at.tune(self, sweeps=sweeps, cache=cache, stream=stream)
+        self.set_config(*res["config"])
+        return res
 
     def close(self):
         if getattr(self, "_h", None):

@@ -1,0 +1,83 @@
+"""Autotuner of the batched persistent engine.
+
+The batch kernel's execution configuration (isg_batch_set_config: CTA shape,
+streams per bundle, generator-state placement) changes its speed but never its
+results, so the tuner can pick it by measurement alone.  It times every
+candidate on a twin of the batch (same samples, seeds and temperatures, a
+separate copy of the state), so the batch's own trajectories are not touched,
+and keeps the fastest.  Choices are cached in a JSON file keyed by GPU name,
+generator kind and the batch's mix of lattice sizes.
+"""
+from __future__ import annotations
+
+import collections
+import json
+import os
+
+# (shape, capacity, resident); capacity 0 = the shape's warps
+SHAPE_WARPS = {0: 32, 1: 24, 2: 16, 3: 16}
+
+
+def candidates() -> list:
+    out = []
+    for shape, warps in SHAPE_WARPS.items():
+        for cap in (warps, warps // 2):
+            for resident in (1, 0):
+                out.append((shape, cap, resident))
+    return out
+
+
+def cache_key(batch) -> str:
+    import torch
+    mix = collections.Counter(batch.L)
+    sizes = ",".join("%dx%d" % (L, n) for L, n in sorted(mix.items()))
+    return "%s|kind%d|%s" % (torch.cuda.get_device_name(), batch.kind, sizes)
+
+
+def _load(cache):
+    if cache and os.path.exists(cache):
+        try:
+            with open(cache) as f:
+                return json.load(f)
+        except (OSError, ValueError):
+            return {}
+    return {}
+
+
+def tune(batch, sweeps: int = 8, cache: str = None, stream=None) -> dict:
+    """Time every candidate for `sweeps` sweeps (one persistent launch, after a
+    warm-up launch that also captures its graph) on a twin of `batch`; return
+    {"config", "psflip", "table", "key", "cached"}.  With `cache`, a stored
+    choice for the same key is returned without measuring, and new choices are
+    stored."""
+    import torch
+    key = cache_key(batch)
+    store = _load(cache)
+    if key in store:
+        hit = store[key]
+        return {"config": tuple(hit["config"]), "psflip": hit["psflip"], "table": hit.get("table", []),
+                "key": key, "cached": True}
+    twin = batch.twin()
+    attempts = twin.info()["attempts_per_sweep"]
+    st = stream if stream is not None else torch.cuda.current_stream()
+    table = []
+    try:
+        for cand in candidates():
+            twin.set_config(*cand)
+            twin.run(sweeps, sweeps, st)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            twin.run(sweeps, sweeps, st)
+            e1.record(st)
+            torch.cuda.synchronize()
+            table.append((cand, e0.elapsed_time(e1) * 1e9 / (sweeps * attempts)))
+    finally:
+        twin.close()
+    best, ps = min(table, key=lambda x: x[1])
+    res = {"config": best, "psflip": ps, "table": [[list(c), p] for c, p in table], "key": key, "cached": False}
+    if cache:
+        store[key] = {"config": list(best), "psflip": ps, "table": res["table"]}
+        os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
+        with open(cache, "w") as f:
+            json.dump(store, f, indent=1)
+    return res

@@ -20,6 +20,7 @@
 // site to stream and draw), which the tests check against isg_sweep and the
 // CPU oracle.
 #include <algorithm>
+#include <type_traits>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -37,6 +38,7 @@ struct isg_batch {
     unsigned* d_ctr = nullptr;          // [0] next bundle, [1] CTAs done
     int nbundles = 0;
     int64_t attempts_per_sweep = 0;
+    isg::BundleConfig cfg;              // execution configuration (isg_batch_set_config)
     cudaStream_t cap = nullptr;         // private stream used for graph capture
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
@@ -45,7 +47,6 @@ struct isg_batch {
 
 namespace isg {
 
-constexpr int kBatchWarps = 32;
 constexpr int kBatchSlack = 512;  // MT19937 window per warp: 624 + 512 words (32 warps fit 227 KiB)
 
 struct BatchArgs {
@@ -55,11 +56,19 @@ struct BatchArgs {
     const int* bsweeps;   // sweeps of each bundle in this launch, or NULL: `sweeps` for all
     int nbundles;
     int sweeps;
+    int resident;         // keep the generator state of bundles that fit in the CTA for the whole launch
     unsigned* ctr;
 };
 
-template <int KIND>
-__global__ void __launch_bounds__(kBatchWarps * 32, 1) batch_kernel(BatchArgs b, StreamConst k) {
+// CTA shapes of the bundle kernel (warps per CTA, CTAs per SM); see BundleConfig.
+struct BundleShape {
+    int warps, per_sm;
+};
+constexpr BundleShape kBundleShapes[kBundleShapeCount] = {{32, 1}, {24, 1}, {16, 1}, {16, 2}};
+
+template <int KIND, int WARPS, int PER_SM>
+__global__ void __launch_bounds__(WARPS * 32, PER_SM) batch_kernel(BatchArgs b, StreamConst k) {
+    constexpr int kBatchWarps = WARPS;
     extern __shared__ uint32_t smem[];
     __shared__ int s_bundle;
     constexpr int kRing = KIND == ISG_RNG_MT19937 ? mt_window(kBatchSlack) : 0;
@@ -74,7 +83,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) batch_kernel(BatchArgs b,
         if (bid >= b.nbundles) break;
         const int e0 = b.boff[bid], n = b.boff[bid + 1] - e0;
         const int sweeps = b.bsweeps ? b.bsweeps[bid] : b.sweeps;
-        const bool resident = n <= kBatchWarps;
+        const bool resident = b.resident && n <= kBatchWarps;
         StreamRegs st;
         if (resident && wid < n) {
             const int2 e = b.entries[e0 + wid];
@@ -111,21 +120,36 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) batch_kernel(BatchArgs b,
     }
 }
 
-static size_t batch_smem(int kind) {
+static size_t batch_smem(int kind, int warps) {
     const int ring = kind == ISG_RNG_MT19937 ? mt_window(kBatchSlack) : 0;
-    return (size_t)kBatchWarps * (ring + 2 * kCondWords) * sizeof(uint32_t);
+    return (size_t)warps * (ring + 2 * kCondWords) * sizeof(uint32_t);
 }
 
-cudaError_t prepare_bundle_kernel(int kind) {
-    const int smem = (int)batch_smem(kind);
+// f(std::integral_constant<int, shape index>) for a runtime shape index.
+template <class F>
+static auto with_shape(int shape, F&& f) {
+    switch (shape) {
+        case 1: return f(std::integral_constant<int, 1>{});
+        case 2: return f(std::integral_constant<int, 2>{});
+        case 3: return f(std::integral_constant<int, 3>{});
+        default: return f(std::integral_constant<int, 0>{});
+    }
+}
+
+cudaError_t prepare_bundle_kernel(int kind, const BundleConfig& cfg) {
     return with_kind(kind, [&](auto kc) {
-        return cudaFuncSetAttribute(batch_kernel<decltype(kc)::value>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    smem);
+        return with_shape(cfg.shape, [&](auto sc) {
+            constexpr BundleShape sh = kBundleShapes[decltype(sc)::value];
+            return cudaFuncSetAttribute(batch_kernel<decltype(kc)::value, sh.warps, sh.per_sm>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)batch_smem(kind, sh.warps));
+        });
     });
 }
 
-cudaError_t launch_bundle_kernel(int kind, const FlipArgs* reps, const int2* entries, const int* boff,
-                                 const int* bsweeps, int nbundles, int sweeps, unsigned* ctr, cudaStream_t s) {
+cudaError_t launch_bundle_kernel(int kind, const BundleConfig& cfg, const FlipArgs* reps, const int2* entries,
+                                 const int* boff, const int* bsweeps, int nbundles, int sweeps, unsigned* ctr,
+                                 cudaStream_t s) {
     if (nbundles <= 0) return cudaSuccess;
     BatchArgs a;
     a.reps = reps;
@@ -134,21 +158,28 @@ cudaError_t launch_bundle_kernel(int kind, const FlipArgs* reps, const int2* ent
     a.bsweeps = bsweeps;
     a.nbundles = nbundles;
     a.sweeps = sweeps;
+    a.resident = cfg.resident;
     a.ctr = ctr;
     const StreamConst k = stream_const();
-    const size_t smem = batch_smem(kind);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = std::max(1, std::min(sms, nbundles));
     return with_kind(kind, [&](auto kc) {
-        batch_kernel<decltype(kc)::value><<<grid, kBatchWarps * 32, smem, s>>>(a, k);
-        return cudaGetLastError();
+        return with_shape(cfg.shape, [&](auto sc) {
+            constexpr BundleShape sh = kBundleShapes[decltype(sc)::value];
+            const int grid = std::max(1, std::min(sms * sh.per_sm, nbundles));
+            batch_kernel<decltype(kc)::value, sh.warps, sh.per_sm>
+                <<<grid, sh.warps * 32, batch_smem(kind, sh.warps), s>>>(a, k);
+            return cudaGetLastError();
+        });
     });
 }
 
+int bundle_warps(const BundleConfig& cfg) { return kBundleShapes[cfg.shape].warps; }
+
 void plan_bundles(const std::vector<isg_sim*>& reps, std::vector<int2>& entries, std::vector<int>& boff,
-                  std::vector<int>* order) {
+                  std::vector<int>* order, int capacity) {
+    const int cap = capacity;  // streams per packed bundle
     struct Bundle {
         std::vector<int2> e;
         std::vector<int> members;
@@ -159,11 +190,11 @@ void plan_bundles(const std::vector<isg_sim*>& reps, std::vector<int2>& entries,
     const int nrep = (int)reps.size();
     for (int r = 0; r < nrep; ++r) {
         const isg_sim* h = reps[r];
-        if (h->S > kBatchWarps) {
+        if (h->S > cap) {
             Bundle bd;
             for (int64_t t = 0; t < h->S; ++t) bd.e.push_back(make_int2(r, (int)t));
             bd.members.push_back(r);
-            bd.work = (double)((h->S + kBatchWarps - 1) / kBatchWarps) * (double)h->R * h->half;
+            bd.work = (double)((h->S + cap - 1) / cap) * (double)h->R * h->half;
             bundles.push_back(bd);
         } else {
             small.push_back(r);
@@ -179,7 +210,7 @@ void plan_bundles(const std::vector<isg_sim*>& reps, std::vector<int2>& entries,
         const isg_sim* h = reps[r];
         Bundle* fit = nullptr;
         for (Bundle& p : packs)
-            if ((int64_t)p.e.size() + h->S <= kBatchWarps) { fit = &p; break; }
+            if ((int64_t)p.e.size() + h->S <= cap) { fit = &p; break; }
         if (!fit) { packs.push_back(Bundle{{}, {}, 0.0}); fit = &packs.back(); }
         for (int64_t t = 0; t < h->S; ++t) fit->e.push_back(make_int2(r, (int)t));
         fit->members.push_back(r);
@@ -201,8 +232,32 @@ void plan_bundles(const std::vector<isg_sim*>& reps, std::vector<int2>& entries,
 }
 
 static cudaError_t batch_launch(isg_batch* b, int sweeps, cudaStream_t s) {
-    return launch_bundle_kernel(b->kind, b->d_reps, b->d_entries, b->d_boff, nullptr, b->nbundles, sweeps,
+    return launch_bundle_kernel(b->kind, b->cfg, b->d_reps, b->d_entries, b->d_boff, nullptr, b->nbundles, sweeps,
                                 b->d_ctr, s);
+}
+
+// Bundles for the configuration's capacity, uploaded (the entries keep their
+// number; the offsets are reallocated); the captured graph is dropped.
+static int batch_plan(isg_batch* b) {
+    std::vector<int2> entries;
+    std::vector<int> boff;
+    plan_bundles(b->reps, entries, boff, nullptr, b->cfg.capacity);
+    isg_sim* h0 = b->reps[0];
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    b->graph_group = 0;
+    dev_free(h0, b->d_boff);
+    b->d_boff = (int*)dev_alloc(h0, boff.size() * sizeof(int));
+    if (!b->d_entries) b->d_entries = (int2*)dev_alloc(h0, entries.size() * sizeof(int2));
+    if (!b->d_boff || !b->d_entries) {
+        set_error("isg_batch: device allocation failed");
+        return ISG_ERR_NOMEM;
+    }
+    b->nbundles = (int)boff.size() - 1;
+    cudaError_t e = cudaMemcpy(b->d_entries, entries.data(), entries.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_boff, boff.data(), boff.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = prepare_bundle_kernel(b->kind, b->cfg);
+    return e == cudaSuccess ? ISG_OK : cuda_fail(e, "isg_batch: bundle plan");
 }
 
 static void batch_free(isg_batch* b) {
@@ -252,30 +307,23 @@ int isg_batch_create(int n, const int* L, const uint64_t* seed_J, const uint64_t
         b->attempts_per_sweep += (int64_t)L[s] * L[s] * L[s];
     }
 
-    // bundles: big lattices alone, small ones first-fit into 32 entries
-    std::vector<int2> entries;
-    std::vector<int> boff;
-    plan_bundles(b->reps, entries, boff, nullptr);
-    b->nbundles = (int)boff.size() - 1;
-
+    // bundles: big lattices alone, small ones first-fit into `capacity` entries
     std::vector<FlipArgs> desc(2 * n);
     for (int r = 0; r < 2 * n; ++r) desc[r] = make_flip_args(b->reps[r], 0);
     isg_sim* h0 = b->reps[0];
     b->d_reps = (FlipArgs*)dev_alloc(h0, desc.size() * sizeof(FlipArgs));
-    b->d_entries = (int2*)dev_alloc(h0, entries.size() * sizeof(int2));
-    b->d_boff = (int*)dev_alloc(h0, boff.size() * sizeof(int));
     b->d_ctr = (unsigned*)dev_alloc(h0, 2 * sizeof(unsigned));
-    if (!b->d_reps || !b->d_entries || !b->d_boff || !b->d_ctr) {
+    if (!b->d_reps || !b->d_ctr) {
         batch_free(b);
         set_error("isg_batch_create: device allocation failed");
         return ISG_ERR_NOMEM;
     }
+    if (const int rc = batch_plan(b)) {
+        batch_free(b);
+        return rc;
+    }
     cudaError_t e = cudaMemcpy(b->d_reps, desc.data(), desc.size() * sizeof(FlipArgs), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(b->d_entries, entries.data(), entries.size() * sizeof(int2), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(b->d_boff, boff.data(), boff.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(b->d_ctr, 0, 2 * sizeof(unsigned));
-    if (e == cudaSuccess) e = prepare_bundle_kernel(rng_kind);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         batch_free(b);
@@ -296,6 +344,34 @@ int isg_batch_info(const isg_batch* b, int* samples, int* bundles, int64_t* atte
     if (samples) *samples = b->n;
     if (bundles) *bundles = b->nbundles;
     if (attempts_per_sweep) *attempts_per_sweep = b->attempts_per_sweep;
+    return ISG_OK;
+}
+
+int isg_batch_set_config(isg_batch* b, int shape, int capacity, int resident) {
+    if (!b || shape < 0 || shape >= kBundleShapeCount || capacity < 0 || (resident != 0 && resident != 1)) {
+        set_error("isg_batch_set_config: bad argument");
+        return ISG_ERR_ARG;
+    }
+    BundleConfig cfg;
+    cfg.shape = shape;
+    const int warps = bundle_warps(cfg);
+    cfg.capacity = capacity == 0 ? warps : capacity;
+    cfg.resident = resident;
+    if (cfg.capacity > warps) {
+        set_error("isg_batch_set_config: capacity %d exceeds the %d warps of shape %d", capacity, warps, shape);
+        return ISG_ERR_ARG;
+    }
+    const cudaError_t e = cudaDeviceSynchronize();  // no launch of the old plan may be in flight
+    if (e != cudaSuccess) return cuda_fail(e, "isg_batch_set_config");
+    b->cfg = cfg;
+    return batch_plan(b);
+}
+
+int isg_batch_get_config(const isg_batch* b, int* shape, int* capacity, int* resident) {
+    if (!b) { set_error("isg_batch_get_config: NULL batch"); return ISG_ERR_ARG; }
+    if (shape) *shape = b->cfg.shape;
+    if (capacity) *capacity = b->cfg.capacity;
+    if (resident) *resident = b->cfg.resident;
     return ISG_OK;
 }
 

@@ -8,23 +8,42 @@
 
 namespace isg {
 
+// Execution configuration of the persistent bundle kernel.  None of it changes
+// a result: every lattice follows its own trajectory whatever the bundles.
+//   shape     0: one CTA of 32 warps per SM, 1: one of 24, 2: one of 16,
+//             3: two of 16
+//   capacity  streams per packed bundle of small lattices (1 .. warps of the shape)
+//   resident  1: the generator state of a bundle that fits in the CTA stays in
+//             shared memory / registers for the whole launch; 0: it is loaded
+//             and stored around every colour pass
+constexpr int kBundleShapeCount = 4;
+struct BundleConfig {
+    int shape = 0;
+    int capacity = 32;
+    int resident = 1;
+};
+
+// Warps per CTA of the configuration's shape.
+int bundle_warps(const BundleConfig& cfg);
+
 // Pack the RNG streams of the lattices `reps` into bundles: a lattice with more
-// than 32 streams is one bundle; smaller lattices are packed first-fit, at most
-// 32 streams per bundle.  Bundles come out largest first.  entries holds
+// than `capacity` streams is one bundle; smaller lattices are packed first-fit,
+// at most `capacity` streams per bundle.  Bundles come out largest first.  entries holds
 // (lattice index, stream) pairs, boff the bundle offsets (size bundles + 1);
 // if order is given it receives the lattice indices of each bundle, each
 // bundle's list terminated by -1.
 void plan_bundles(const std::vector<isg_sim*>& reps, std::vector<int2>& entries, std::vector<int>& boff,
-                  std::vector<int>* order);
+                  std::vector<int>* order, int capacity = 32);
 
 // One-time attribute set-up of the bundle kernel (large dynamic shared memory).
-cudaError_t prepare_bundle_kernel(int kind);
+cudaError_t prepare_bundle_kernel(int kind, const BundleConfig& cfg);
 
-// Launch the persistent bundle kernel: one CTA per SM (at most one per bundle)
-// sweeps bundle after bundle; bundle b runs bsweeps[b] sweeps (or `sweeps` for
-// all when bsweeps is NULL).  ctr must hold two zeroed words; the kernel
-// returns them to zero when it ends.
-cudaError_t launch_bundle_kernel(int kind, const FlipArgs* reps, const int2* entries, const int* boff,
-                                 const int* bsweeps, int nbundles, int sweeps, unsigned* ctr, cudaStream_t s);
+// Launch the persistent bundle kernel: the shape's CTAs per SM (at most one per
+// bundle) sweep bundle after bundle; bundle b runs bsweeps[b] sweeps (or
+// `sweeps` for all when bsweeps is NULL).  ctr must hold two zeroed words; the
+// kernel returns them to zero when it ends.
+cudaError_t launch_bundle_kernel(int kind, const BundleConfig& cfg, const FlipArgs* reps, const int2* entries,
+                                 const int* boff, const int* bsweeps, int nbundles, int sweeps, unsigned* ctr,
+                                 cudaStream_t s);
 
 }  // namespace isg

@@ -147,7 +147,7 @@ static int launch_batched(isg_server* s, int kind, const std::vector<int>& activ
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(P.bsweeps, P.h_bsweeps.data(), P.h_bsweeps.size() * sizeof(int), cudaMemcpyHostToDevice,
                             st);
-    if (e == cudaSuccess) e = launch_bundle_kernel(kind, P.reps, P.entries, P.boff, P.bsweeps, nb, 0, P.ctr, st);
+    if (e == cudaSuccess) e = launch_bundle_kernel(kind, BundleConfig{}, P.reps, P.entries, P.boff, P.bsweeps, nb, 0, P.ctr, st);
     if (e != cudaSuccess) return cuda_fail(e, "isg_server_run: batched quantum");
     return ISG_OK;
 }
@@ -191,7 +191,7 @@ int isg_server_create(size_t hbm_budget_bytes, int quantum_sweeps, int max_activ
             if (!s->plan[k].ctr) e = cudaErrorMemoryAllocation;
         }
         if (e == cudaSuccess) e = cudaMemset(s->plan[k].ctr, 0, 2 * sizeof(unsigned));
-        if (e == cudaSuccess) e = prepare_bundle_kernel(k);
+        if (e == cudaSuccess) e = prepare_bundle_kernel(k, BundleConfig{});
     }
     for (int k = 0; k < kWideStreams && e == cudaSuccess; ++k)
         e = cudaStreamCreateWithFlags(&s->wide_stream[k], cudaStreamNonBlocking);

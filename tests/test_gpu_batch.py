@@ -110,3 +110,65 @@ def test_batch_rejects_bad_arguments(isg):
         isg.Batch([16, 15], [1, 2], [1, 2, 3, 4], [1.0, 1.0])
     with pytest.raises(isg.IsgError):
         isg.Batch([16], [1], [1, 2], [0.0])
+
+
+@pytest.mark.parametrize("kind", ["mt19937", "minstd", "parisi_rapuano"])
+def test_every_execution_configuration_gives_identical_states(isg, kind):
+    """Layout and tuning invariance: each candidate the autotuner may pick (CTA
+    shape, streams per bundle, generator-state placement) sweeps the same mixed
+    batch to bit-identical states (energies and hashes of every replica), also
+    when the configuration changes between groups of sweeps."""
+    from paper_1411_0127_gb300 import autotune
+    L, J, S, B = mixed()
+    ref = isg.Batch(L, J, S, B, kind)
+    ref.run(6, 3)
+    E0, H0 = ref.tracked()
+    ref.close()
+    cands = autotune.candidates()
+    for cand in cands:
+        b = isg.Batch(L, J, S, B, kind)
+        b.set_config(*cand)
+        assert b.get_config() == (cand[0], cand[1], cand[2])
+        b.run(6, 3)
+        E, H = b.tracked()
+        assert np.array_equal(E, E0) and np.array_equal(H, H0), cand
+        b.close()
+    # switching configurations mid-run
+    b = isg.Batch(L, J, S, B, kind)
+    for i, cand in enumerate(cands[:3]):
+        b.set_config(*cand)
+        b.run(2, 2)
+    E, H = b.tracked()
+    assert np.array_equal(E, E0) and np.array_equal(H, H0)
+    Em, _ = b.measure()
+    assert np.array_equal(Em, E0)
+    b.close()
+
+
+def test_autotuner_picks_a_candidate_and_caches_it(isg, tmp_path):
+    from paper_1411_0127_gb300 import autotune
+    L, J, S, B = mixed()
+    b = isg.Batch(L, J, S, B, "mt19937")
+    b.run(2, 2)
+    E0, H0 = b.tracked()
+    cache = str(tmp_path / "tune.json")
+    res = b.autotune(sweeps=2, cache=cache)
+    assert not res["cached"]
+    assert tuple(res["config"]) in autotune.candidates()
+    assert len(res["table"]) == len(autotune.candidates())
+    assert b.get_config() == tuple(res["config"])
+    E1, H1 = b.tracked()                               # the tuner ran on a twin
+    assert np.array_equal(E1, E0) and np.array_equal(H1, H0)
+    again = b.autotune(sweeps=2, cache=cache)
+    assert again["cached"] and tuple(again["config"]) == tuple(res["config"])
+    b.close()
+
+
+def test_batch_config_rejects_bad_values(isg):
+    L, J, S, B = mixed()
+    b = isg.Batch(L[:2], J[:2], S[:4], B[:2], "minstd")
+    for bad in [(4, 0, 1), (-1, 0, 1), (2, 17, 1), (0, 33, 1), (0, 8, 2)]:
+        with pytest.raises(isg.IsgError):
+            b.set_config(*bad)
+    assert b.get_config() == (0, 32, 1)
+    b.close()
