@@ -209,10 +209,22 @@ def cpu_baseline(w, target_s: float = 12.0) -> dict:
         attempts += 2 * n
         t0 = t1
     dt = time.perf_counter() - t_start
+    # the same on one core, for about a quarter of the time
+    t_single, att1, t1s = time.perf_counter(), 0, 0
+    while time.perf_counter() - t_single < target_s / 4:
+        t1s, t1e, n = _stream_block(S, R, w.L, t1s, 1)
+        o.pass_range(0, t1s, t1e, 1)
+        o.pass_range(1, t1s, t1e, 1)
+        att1 += 2 * n
+        t1s = t1e
+    dt1 = time.perf_counter() - t_single
     o.close()
     return {"value": dt * 1e12 / attempts, "unit": UNIT, "cores": min(threads, m), "kind": "oracle",
             "sample": "red+blue passes over blocks of %d of the %d streams of the L=%d lattice (%d attempts, "
-                      "%.1f s wall)" % (m, S, w.L, attempts, dt)}
+                      "%.1f s wall)" % (m, S, w.L, attempts, dt),
+            "single_core": {"value": dt1 * 1e12 / att1, "unit": UNIT, "cores": 1,
+                            "sample": "red+blue passes over one stream at a time (%d attempts, %.1f s wall)"
+                                      % (att1, dt1)}}
 
 
 def batched_section(a, stream) -> dict:
