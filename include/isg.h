@@ -210,9 +210,10 @@ int isg_batch_get_config(const isg_batch *b, int *shape, int *capacity, int *res
 int isg_batch_member(isg_batch *b, int i, isg_sim **out);
 
 /* Enqueue `sweeps` sweeps of every replica (async).  The work runs as persistent
- * launches of group_sweeps sweeps (<= 0 picks 64): one CTA per SM takes bundle
- * after bundle; the group launch is captured once into a CUDA graph and
- * replayed; a remainder of sweeps % group_sweeps is launched directly. */
+ * launches of group_sweeps sweeps (<= 0 picks 64): the CTAs of the execution
+ * configuration (isg_batch_set_config) take bundle after bundle; the group
+ * launch is captured once into a CUDA graph and replayed; a remainder of
+ * sweeps % group_sweeps is launched directly. */
 int isg_batch_run(isg_batch *b, int64_t sweeps, int group_sweeps, void *cuda_stream);
 
 /* Energies from scratch of the 2n replicas (E[2s], E[2s+1]) and overlaps

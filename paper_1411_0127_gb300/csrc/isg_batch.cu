@@ -6,14 +6,17 @@
 // lattices (32-bit words forced, so one kernel template serves every L), two
 // per sample with the same couplings and different spin seeds, and:
 //   * on the host their RNG streams are packed into bundles: a lattice with more
-//     than 32 streams is one bundle; smaller lattices are packed together, at
-//     most 32 streams per bundle;
-//   * one CTA of 32 warps per SM takes bundle after bundle (largest first) from
-//     a counter and runs all sweeps of the launch on it: warp w sweeps entries
-//     w, w + 32, ... of the bundle, and a block barrier separates the colour
-//     passes; no lattice spans two CTAs, so no grid-wide barrier is needed;
-//   * when a bundle has at most 32 streams each warp keeps its stream's MT19937
-//     words in shared memory for the whole launch;
+//     than `capacity` streams is one bundle; smaller lattices are packed
+//     together, at most `capacity` streams per bundle;
+//   * CTAs of WARPS warps (one or two per SM) take bundle after bundle (largest
+//     first) from a counter and run all sweeps of the launch on it: warp w
+//     sweeps entries w, w + WARPS, ... of the bundle, and a block barrier
+//     separates the colour passes; no lattice spans two CTAs, so no grid-wide
+//     barrier is needed;
+//   * when a bundle has at most WARPS streams each warp can keep its stream's
+//     generator state (MT19937 words in shared memory) for the whole launch;
+//   * the shape, the capacity and that residency form the execution
+//     configuration (isg_batch_set_config), chosen by the autotuner;
 //   * the bundle counter returns to zero when the last CTA leaves, so the
 //     launch is captured once into a CUDA graph and replayed.
 // Every lattice follows exactly the trajectory it has alone (same map from
@@ -47,7 +50,7 @@ struct isg_batch {
 
 namespace isg {
 
-constexpr int kBatchSlack = 512;  // MT19937 window per warp: 624 + 512 words (32 warps fit 227 KiB)
+constexpr int kBatchSlack = 512;  // MT19937 window per warp: 624 + 512 words (32 warps fit in 227 KiB)
 
 struct BatchArgs {
     const FlipArgs* reps;

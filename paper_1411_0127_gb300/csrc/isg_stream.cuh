@@ -4,7 +4,8 @@
 // A stream owns R consecutive rows r = y + L*z of a lattice.  The warp walks
 // them in groups of G = 32 / W rows (W words per row and colour), one word of
 // the group per lane:
-//   1. draw phase: the group's draws are produced 128 at a time in stream order
+//   1. draw phase: the group's draws are produced 128 (MT19937 in the latency
+//      form: 224) at a time in stream order
 //      (row by row, ascending x) and compared with the three integer thresholds
 //      thr1 > thr2 > thr3 (Sec. 4: R < Rmax exp(-beta dE)).  Because the three
 //      comparisons are nested, a draw's outcome is a level 0..3 (how many
