@@ -475,6 +475,7 @@ def run_ours(a, dist: Dist):
     hbm_gbs = BYTES_PER_ATTEMPT * attempts_per_launch / launch_s / 1e9
     hbm_pk, hbm_src = hbm_peak()
     traffic = traffic_from_profile(w.kind)
+    int_rates = {name: isg.int_rate(mode) / 1e12 for mode, name in ((0, "lop3_imad"), (1, "lop3"), (2, "imad"))}
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": a.steps,
@@ -493,6 +494,8 @@ def run_ours(a, dist: Dist):
                      "kernel": "flip (one colour pass)", "ops_per_attempt": ops,
                      "attempts_per_launch": attempts_per_launch, "launch_ms": launch_s * 1e3,
                      "peak_source": "derived: 152 SMs x 128 lanes x 2070 MHz",
+                     "measured_int_peaks_tops": int_rates,
+                     "frac_of_measured_lop3_imad": achieved_tops / int_rates["lop3_imad"],
                      "hbm": {"achieved": hbm_gbs, "peak": hbm_pk, "unit": "GB/s", "frac": hbm_gbs / hbm_pk,
                              "peak_source": hbm_src, "bytes_per_attempt": BYTES_PER_ATTEMPT}},
         "clocks": clk,

@@ -308,6 +308,14 @@ int isg_amsc_read_spins(const isg_amsc *m, int sample, int8_t *host_out, size_t 
  * own temporary buffers. */
 int isg_rng_count_odd(int rng_kind, uint64_t seed, int64_t streams, int64_t n, uint64_t *odd, double *gen_ms);
 
+/* Integer issue-rate microbenchmark (a measurement tool, not part of the
+ * method): the 32-bit integer operations per second the GPU sustains on
+ * independent chains of mode 0 = LOP3 and IMAD alternating, 1 = LOP3 only,
+ * 2 = IMAD only, over all SMs (sync; about a millisecond).  These are the
+ * measured counterparts of the derived integer peak of the flip kernel's
+ * roofline. */
+int isg_int_rate(int mode, double *ops_per_s);
+
 /* ------------------------------------------------------- no allocation --- */
 
 /* The energy of Eq. 1, like isg_energy, for callers that must not allocate

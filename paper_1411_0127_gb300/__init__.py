@@ -69,6 +69,7 @@ SIGNATURES = {
     "isg_server_job": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
     "isg_server_stats": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "isg_rng_count_odd": (_i32, [_i32, _u64, _i64, _i64, _vp, _vp]),
+    "isg_int_rate": (_i32, [_i32, _vp]),
     "isg_amsc_create": (_i32, [_i32, _vp, _vp, _u64, _dbl, _i32, _PP]),
     "isg_amsc_destroy": (None, [_vp]),
     "isg_amsc_sweep": (_i32, [_vp, _i64, _vp]),
@@ -85,6 +86,13 @@ def rng_count_odd(rng_kind, seed: int, streams: int, n: int):
     _check(lib().isg_rng_count_odd(kind, int(seed) & (2**64 - 1), int(streams), int(n), ctypes.byref(odd),
                                    ctypes.byref(ms)))
     return odd.value, ms.value
+
+
+def int_rate(mode: int) -> float:
+    """32-bit integer ops/s on independent chains (0: LOP3 + IMAD, 1: LOP3, 2: IMAD)."""
+    v = ctypes.c_double()
+    _check(lib().isg_int_rate(int(mode), ctypes.byref(v)))
+    return v.value
 
 
 class IsgError(RuntimeError):

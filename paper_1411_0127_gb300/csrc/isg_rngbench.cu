@@ -137,3 +137,74 @@ extern "C" int isg_rng_count_odd(int rng_kind, uint64_t seed, int64_t streams, i
     if (gen_ms) *gen_ms = ms;
     return ISG_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Integer issue-rate microbenchmark (the denominators of the flip kernel's
+// roofline): every thread runs 8 independent chains for `iters` steps; a step
+// of a chain is one three-input logic operation (LOP3), one integer
+// multiply-add (IMAD), or one of each.  The chains feed each other's operands
+// so that nothing folds, and their XOR is written out so that nothing is
+// dropped.  Ops counted: chains x steps x (1 or 2) per thread.
+namespace isg {
+
+template <int MODE>
+__global__ void __launch_bounds__(256) int_rate_kernel(uint32_t seed, int iters, uint32_t* out) {
+    uint32_t a[8], b[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        a[j] = seed ^ (threadIdx.x * 0x9E3779B9u + j);
+        b[j] = seed + (blockIdx.x * 0x85EBCA6Bu) + 3 * j;
+    }
+    const uint32_t m = seed | 0x01000193u;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (MODE != 2) a[j] = (a[j] & b[(j + 1) & 7]) ^ b[j];    // one LOP3
+            if (MODE != 1) b[j] = b[j] * m + a[(j + 3) & 7];         // one IMAD
+            if (MODE == 1) b[j] = (b[j] | a[(j + 5) & 7]) ^ a[j];    // LOP3 only: a second LOP3
+            if (MODE == 2) a[j] = a[j] * m + b[(j + 5) & 7];         // IMAD only: a second IMAD
+        }
+    }
+    uint32_t r = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) r ^= a[j] ^ b[j];
+    if (r == 0x5A5A5A5Au) out[0] = r;  // practically never: keeps the chains live
+}
+
+}  // namespace isg
+
+extern "C" int isg_int_rate(int mode, double* ops_per_s) {
+    if (!ops_per_s || mode < 0 || mode > 2) {
+        set_error("isg_int_rate: bad argument");
+        return ISG_ERR_ARG;
+    }
+    uint32_t* d = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    int dev = 0, sms = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int blocks = sms * 8, threads = 256, iters = 4096;
+    float ms = 0.f;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the first launch warms up
+        e = cudaEventRecord(e0, 0);
+        if (e == cudaSuccess) {
+            if (mode == 0) int_rate_kernel<0><<<blocks, threads>>>(0x12345u + rep, iters, d);
+            else if (mode == 1) int_rate_kernel<1><<<blocks, threads>>>(0x12345u + rep, iters, d);
+            else int_rate_kernel<2><<<blocks, threads>>>(0x12345u + rep, iters, d);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, 0);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    }
+    cudaFree(d);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "isg_int_rate");
+    const double ops = (double)blocks * threads * iters * 8 * 2;
+    *ops_per_s = ops / (ms * 1e-3);
+    return ISG_OK;
+}

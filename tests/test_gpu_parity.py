@@ -102,6 +102,17 @@ def test_generator_benchmark_counts(isg, kind, n):
     assert ms >= 0.0
 
 
+def test_integer_rate_microbenchmark(isg):
+    """The measured integer rates are positive and below the issue limit
+    (SMs x 128 lanes x the maximum clock, with 10 % of slack for timing)."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    limit = sms * 128 * 2.1e9 * 1.1
+    for mode in (0, 1, 2):
+        r = isg.int_rate(mode)
+        assert 0 < r < limit, (mode, r)
+
+
 # ------------------------------------------------------------------- init ---
 
 @pytest.mark.parametrize("L", [4, 6, 16, 32, 48, 96, 130])
