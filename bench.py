@@ -256,9 +256,9 @@ def batched_section(a, stream) -> dict:
            "psflip": ms * 1e9 / (sweeps * attempts),
            "samples_sweeps_per_s": len(samples) * sweeps / (ms / 1e3),
            "autotune": {"config": list(tuned["config"]), "candidates": len(tuned["table"]),
-                        "psflip_by_config_8_sweeps": {"%d/%d/%d" % tuple(c): round(p, 4) for c, p in tuned["table"]},
+                        "psflip_by_config_8_sweeps": {"%d/%d/%d/%d" % tuple(c): round(p, 4) for c, p in tuned["table"]},
                         "note": "config = CTA shape (0: 32x1, 1: 24x1, 2: 16x1, 3: 16x2 warps x CTAs per SM) / "
-                                "streams per bundle / resident generator state"}}
+                                "streams per bundle / resident generator state / words per lane"}}
     members = [b.member(r) for r in range(2 * len(samples))]
     for name, fn in (("plain_one_sample_per_launch_psflip", "sweep_plain"),
                      ("fast_one_sample_per_launch_psflip", "sweep")):

@@ -195,14 +195,17 @@ int isg_batch_info(const isg_batch *b, int *samples, int *bundles, int64_t *atte
  *   resident  1: the generator state of a bundle that fits in the CTA stays in
  *             shared memory / registers for a whole launch; 0: it is loaded and
  *             stored around every colour pass
- * Words per thread are fixed: one 32-bit word of a row group per lane.
+ *   words_per_lane  32-bit words of a row group each lane updates, 1 or 2
+ *             (a row group is 32 * words_per_lane words: its draws are made in
+ *             one run, and 2 halves the groups per pass)
  * Synchronises the device, re-plans the bundles and drops the captured graph;
- * ISG_ERR_ARG for an unknown shape, a capacity above the shape's warps or a
- * resident flag other than 0/1.  The default is (0, 32, 1). */
-int isg_batch_set_config(isg_batch *b, int shape, int capacity, int resident);
+ * ISG_ERR_ARG for an unknown shape, a capacity above the shape's warps, a
+ * resident flag other than 0/1 or words_per_lane other than 1/2.  The default
+ * is (0, 32, 1, 1). */
+int isg_batch_set_config(isg_batch *b, int shape, int capacity, int resident, int words_per_lane);
 
 /* The current configuration (any pointer may be NULL). */
-int isg_batch_get_config(const isg_batch *b, int *shape, int *capacity, int *resident);
+int isg_batch_get_config(const isg_batch *b, int *shape, int *capacity, int *resident, int *words_per_lane);
 
 /* Handle of replica i (0 <= i < 2n; replicas 2s, 2s+1 belong to sample s).  The
  * handle stays owned by the batch: use it with the measuring, reading and

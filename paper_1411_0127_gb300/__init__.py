@@ -57,8 +57,8 @@ SIGNATURES = {
     "isg_batch_destroy": (None, [_vp]),
     "isg_batch_info": (_i32, [_vp, _vp, _vp, _vp]),
     "isg_batch_member": (_i32, [_vp, _i32, _PP]),
-    "isg_batch_set_config": (_i32, [_vp, _i32, _i32, _i32]),
-    "isg_batch_get_config": (_i32, [_vp, _vp, _vp, _vp]),
+    "isg_batch_set_config": (_i32, [_vp, _i32, _i32, _i32, _i32]),
+    "isg_batch_get_config": (_i32, [_vp, _vp, _vp, _vp, _vp]),
     "isg_batch_run": (_i32, [_vp, _i64, _i32, _vp]),
     "isg_batch_measure": (_i32, [_vp, _vp, _vp, _vp]),
     "isg_batch_tracked": (_i32, [_vp, _vp, _vp, _vp]),
@@ -349,14 +349,16 @@ class Batch:
         self.beta = [float(v) for v in B]
         self._args = (list(self.L), [int(v) for v in J], [int(v) for v in S], list(self.beta), kind)
 
-    def set_config(self, shape: int, capacity: int = 0, resident: int = 1):
+    def set_config(self, shape: int, capacity: int = 0, resident: int = 1, words_per_lane: int = 1):
         """Execution configuration (see isg_batch_set_config); results do not depend on it."""
-        _check(lib().isg_batch_set_config(self._h, int(shape), int(capacity), int(resident)))
+        _check(lib().isg_batch_set_config(self._h, int(shape), int(capacity), int(resident), int(words_per_lane)))
 
     def get_config(self) -> tuple:
-        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        _check(lib().isg_batch_get_config(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
-        return a.value, b.value, c.value
+        """(shape, capacity, resident, words_per_lane)."""
+        a, b, c, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().isg_batch_get_config(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                          ctypes.byref(d)))
+        return a.value, b.value, c.value, d.value
 
     def twin(self) -> "Batch":
         """A new batch with the same samples, seeds, temperatures and kind, at

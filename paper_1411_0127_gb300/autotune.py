@@ -1,7 +1,7 @@
 """Autotuner of the batched persistent engine.
 
 The batch kernel's execution configuration (isg_batch_set_config: CTA shape,
-streams per bundle, generator-state placement) changes its speed but never its
+streams per bundle, generator-state placement, words per lane) changes its speed but never its
 results, so the tuner can pick it by measurement alone.  It times every
 candidate on a twin of the batch (same samples, seeds and temperatures, a
 separate copy of the state), so the batch's own trajectories are not touched,
@@ -14,7 +14,7 @@ import collections
 import json
 import os
 
-# (shape, capacity, resident); capacity 0 = the shape's warps
+# (shape, capacity, resident, words per lane); see isg_batch_set_config
 SHAPE_WARPS = {0: 32, 1: 24, 2: 16, 3: 16}
 
 
@@ -23,7 +23,8 @@ def candidates() -> list:
     for shape, warps in SHAPE_WARPS.items():
         for cap in (warps, warps // 2):
             for resident in (1, 0):
-                out.append((shape, cap, resident))
+                for wpt in (1, 2):
+                    out.append((shape, cap, resident, wpt))
     return out
 
 

@@ -69,14 +69,14 @@ struct BundleShape {
 };
 constexpr BundleShape kBundleShapes[kBundleShapeCount] = {{32, 1}, {24, 1}, {16, 1}, {16, 2}};
 
-template <int KIND, int WARPS, int PER_SM>
+template <int KIND, int WARPS, int PER_SM, int WPT>
 __global__ void __launch_bounds__(WARPS * 32, PER_SM) batch_kernel(BatchArgs b, StreamConst k) {
     constexpr int kBatchWarps = WARPS;
     extern __shared__ uint32_t smem[];
     __shared__ int s_bundle;
     constexpr int kRing = KIND == ISG_RNG_MT19937 ? mt_window(kBatchSlack) : 0;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    uint32_t* ring = smem + wid * (kRing + 2 * kCondWords);
+    uint32_t* ring = smem + wid * (kRing + 2 * WPT * kCondWords);
     uint32_t* cond = ring + kRing;
     for (;;) {
         if (threadIdx.x == 0) s_bundle = (int)atomicAdd(&b.ctr[0], 1u);
@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(WARPS * 32, PER_SM) batch_kernel(BatchArgs b, 
                 if (!resident) load_stream<KIND>(a, e.y, ring, st, k, lane);
                 int dE = 0;
                 const int64_t rb = (int64_t)e.y * a.R, re = rb + a.R < a.rows ? rb + a.R : a.rows;
-                stream_pass<uint32_t, KIND, kBatchSlack, true>(a, pass & 1, rb, re, ring, cond, st, k, lane, dE);
+                stream_pass<uint32_t, KIND, kBatchSlack, true, WPT>(a, pass & 1, rb, re, ring, cond, st, k, lane, dE);
                 if (!resident) store_stream<KIND>(a, e.y, ring, st, lane);
                 for (int sh = 16; sh; sh >>= 1) dE += __shfl_xor_sync(kFull, dE, sh);
                 if (lane == 0 && dE != 0) atomicAdd((unsigned long long*)a.dE, (unsigned long long)(long long)dE);
@@ -123,9 +123,9 @@ __global__ void __launch_bounds__(WARPS * 32, PER_SM) batch_kernel(BatchArgs b, 
     }
 }
 
-static size_t batch_smem(int kind, int warps) {
+static size_t batch_smem(int kind, int warps, int wpt) {
     const int ring = kind == ISG_RNG_MT19937 ? mt_window(kBatchSlack) : 0;
-    return (size_t)warps * (ring + 2 * kCondWords) * sizeof(uint32_t);
+    return (size_t)warps * (ring + 2 * wpt * kCondWords) * sizeof(uint32_t);
 }
 
 // f(std::integral_constant<int, shape index>) for a runtime shape index.
@@ -139,13 +139,22 @@ static auto with_shape(int shape, F&& f) {
     }
 }
 
+// f(std::integral_constant<int, words per lane>) for a runtime value of 1 or 2.
+template <class F>
+static auto with_wpt(int wpt, F&& f) {
+    if (wpt == 2) return f(std::integral_constant<int, 2>{});
+    return f(std::integral_constant<int, 1>{});
+}
+
 cudaError_t prepare_bundle_kernel(int kind, const BundleConfig& cfg) {
     return with_kind(kind, [&](auto kc) {
         return with_shape(cfg.shape, [&](auto sc) {
-            constexpr BundleShape sh = kBundleShapes[decltype(sc)::value];
-            return cudaFuncSetAttribute(batch_kernel<decltype(kc)::value, sh.warps, sh.per_sm>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)batch_smem(kind, sh.warps));
+            return with_wpt(cfg.wpt, [&](auto wc) {
+                constexpr BundleShape sh = kBundleShapes[decltype(sc)::value];
+                return cudaFuncSetAttribute(
+                    batch_kernel<decltype(kc)::value, sh.warps, sh.per_sm, decltype(wc)::value>,
+                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem(kind, sh.warps, decltype(wc)::value));
+            });
         });
     });
 }
@@ -169,11 +178,14 @@ cudaError_t launch_bundle_kernel(int kind, const BundleConfig& cfg, const FlipAr
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     return with_kind(kind, [&](auto kc) {
         return with_shape(cfg.shape, [&](auto sc) {
-            constexpr BundleShape sh = kBundleShapes[decltype(sc)::value];
-            const int grid = std::max(1, std::min(sms * sh.per_sm, nbundles));
-            batch_kernel<decltype(kc)::value, sh.warps, sh.per_sm>
-                <<<grid, sh.warps * 32, batch_smem(kind, sh.warps), s>>>(a, k);
-            return cudaGetLastError();
+            return with_wpt(cfg.wpt, [&](auto wc) {
+                constexpr BundleShape sh = kBundleShapes[decltype(sc)::value];
+                constexpr int wpt = decltype(wc)::value;
+                const int grid = std::max(1, std::min(sms * sh.per_sm, nbundles));
+                batch_kernel<decltype(kc)::value, sh.warps, sh.per_sm, wpt>
+                    <<<grid, sh.warps * 32, batch_smem(kind, sh.warps, wpt), s>>>(a, k);
+                return cudaGetLastError();
+            });
         });
     });
 }
@@ -350,13 +362,15 @@ int isg_batch_info(const isg_batch* b, int* samples, int* bundles, int64_t* atte
     return ISG_OK;
 }
 
-int isg_batch_set_config(isg_batch* b, int shape, int capacity, int resident) {
-    if (!b || shape < 0 || shape >= kBundleShapeCount || capacity < 0 || (resident != 0 && resident != 1)) {
+int isg_batch_set_config(isg_batch* b, int shape, int capacity, int resident, int words_per_lane) {
+    if (!b || shape < 0 || shape >= kBundleShapeCount || capacity < 0 || (resident != 0 && resident != 1) ||
+        (words_per_lane != 1 && words_per_lane != 2)) {
         set_error("isg_batch_set_config: bad argument");
         return ISG_ERR_ARG;
     }
     BundleConfig cfg;
     cfg.shape = shape;
+    cfg.wpt = words_per_lane;
     const int warps = bundle_warps(cfg);
     cfg.capacity = capacity == 0 ? warps : capacity;
     cfg.resident = resident;
@@ -370,11 +384,12 @@ int isg_batch_set_config(isg_batch* b, int shape, int capacity, int resident) {
     return batch_plan(b);
 }
 
-int isg_batch_get_config(const isg_batch* b, int* shape, int* capacity, int* resident) {
+int isg_batch_get_config(const isg_batch* b, int* shape, int* capacity, int* resident, int* words_per_lane) {
     if (!b) { set_error("isg_batch_get_config: NULL batch"); return ISG_ERR_ARG; }
     if (shape) *shape = b->cfg.shape;
     if (capacity) *capacity = b->cfg.capacity;
     if (resident) *resident = b->cfg.resident;
+    if (words_per_lane) *words_per_lane = b->cfg.wpt;
     return ISG_OK;
 }
 

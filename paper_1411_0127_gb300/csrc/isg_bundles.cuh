@@ -16,11 +16,14 @@ namespace isg {
 //   resident  1: the generator state of a bundle that fits in the CTA stays in
 //             shared memory / registers for the whole launch; 0: it is loaded
 //             and stored around every colour pass
+//   wpt       words of a row group each lane updates (1 or 2): a row group is
+//             wpt * 32 words, so 2 halves the groups per pass
 constexpr int kBundleShapeCount = 4;
 struct BundleConfig {
     int shape = 0;
     int capacity = 32;
     int resident = 1;
+    int wpt = 1;
 };
 
 // Warps per CTA of the configuration's shape.

@@ -243,7 +243,7 @@ __device__ __forceinline__ void word_load(const FlipArgs& a, int c, int r, int y
 
 template <typename Word>
 __device__ __forceinline__ void word_compute(const FlipArgs& a, int c, const WordIn<Word>& q, int k,
-                                             const uint32_t* cond, int off, int& dEsum) {
+                                             const uint32_t* cond, int off, int& dEsum, int hi_off = kCondWords) {
     constexpr int w = 8 * sizeof(Word);
     const int W = a.W, nt = a.nt;
     Word* Sc = (Word*)(a.planes + (size_t)(4 * c) * (size_t)a.plane_bytes);
@@ -263,7 +263,7 @@ __device__ __forceinline__ void word_compute(const FlipArgs& a, int c, const Wor
     Word u0, u1, u2;
     Logic<Word>::count6(e_xp, e_xm, e_yp, e_ym, e_zp, e_zm, u0, u1, u2);
     const Word lo = take_bits<Word>(cond, off);
-    const Word hi = take_bits<Word>(cond + kCondWords, off);
+    const Word hi = take_bits<Word>(cond + hi_off, off);
     Word f = Logic<Word>::flip(u0, u1, u2, lo | hi, hi, lo & hi);
     if (k == W - 1 && nt < w) f &= (Word)((Word(1) << nt) - 1);
     Sc[q.o] = s ^ f;
@@ -272,10 +272,10 @@ __device__ __forceinline__ void word_compute(const FlipArgs& a, int c, const Wor
 
 template <typename Word>
 __device__ __forceinline__ void word_update(const FlipArgs& a, int c, int r, int y, int z, int k,
-                                            const uint32_t* cond, int off, int& dEsum) {
+                                            const uint32_t* cond, int off, int& dEsum, int hi_off = kCondWords) {
     WordIn<Word> q;
     word_load<Word>(a, c, r, y, z, k, q);
-    word_compute<Word>(a, c, q, k, cond, off, dEsum);
+    word_compute<Word>(a, c, q, k, cond, off, dEsum, hi_off);
 }
 
 // Generator state of the stream a warp is working on.
@@ -373,17 +373,21 @@ __device__ __forceinline__ void level_ballots(const uint32_t (&d)[N], const Cmp&
 // or a segment that starts at a row group); the generator state, positioned at
 // the first of these rows, is in B / st.  SLACK is the free space of the
 // MT19937 window (see mt_window); TRIM selects the throughput form of the draw
-// phase (level_ballots; MINSTD four blocks per step) over the shorter-latency
-// one (MINSTD two blocks per step).
-template <typename Word, int KIND, int SLACK, bool TRIM>
+// phase (level_ballots; MINSTD four blocks per step) over the latency one
+// (MINSTD two blocks per step, MT19937 seven, the word-update loads issued
+// before the draws).  WPT is the number of words of a row group each lane
+// updates: a group is WPT * 32 / W rows, and cond holds two bit streams of
+// WPT * kCondWords words each.
+template <typename Word, int KIND, int SLACK, bool TRIM, int WPT = 1>
 __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t r_begin, int64_t r_end, uint32_t* B,
                                             uint32_t* cond, StreamRegs& st, const StreamConst& k, int lane,
                                             int& dEsum) {
     constexpr int w = 8 * sizeof(Word);
     constexpr bool kMT = KIND == ISG_RNG_MT19937;
+    constexpr int kCond = WPT * kCondWords;
     const int W = a.W, half = a.half, L = a.L;
     const Cmp cm = cmp_of(a);
-    const int G = 32 / W;
+    const int G = WPT * 32 / W;
     const int lj = lane / W, lk = lane - lj * W;
     const int loff = lj * half + lk * w;
     int r = (int)r_begin + lj;
@@ -395,7 +399,7 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t r_
         // latency form: the group's plane words are loaded before its draws are made
         WordIn<Word> win;
         const bool act = lane < nrows * W;
-        if (!TRIM && act) word_load<Word>(a, c, r, y, z, lk, win);
+        if (!TRIM && WPT == 1 && act) word_load<Word>(a, c, r, y, z, lk, win);
         // draws four 32-draw blocks per step (MINSTD without TRIM: two), then the
         // remaining blocks one by one
         int b = 0;  // 32-draw blocks of this group done so far
@@ -414,7 +418,7 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t r_
                     }
                 if (lane < 7) {
                     cond[7 * q + lane] = l;
-                    cond[kCondWords + 7 * q + lane] = h;
+                    cond[kCond + 7 * q + lane] = h;
                 }
             }
             b = 7 * nsev;
@@ -427,7 +431,7 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t r_
                 level_ballots<2, false>(d, cm, lo, hi);
                 if (lane == 0) {
                     *(uint2*)(cond + 2 * q) = make_uint2(lo[0], lo[1]);
-                    *(uint2*)(cond + kCondWords + 2 * q) = make_uint2(hi[0], hi[1]);
+                    *(uint2*)(cond + kCond + 2 * q) = make_uint2(hi[0], hi[1]);
                 }
             }
             b = 2 * npairs;
@@ -451,7 +455,7 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t r_
                 level_ballots<4, TRIM>(d, cm, lo, hi);
                 if (lane == 0) {
                     *(uint4*)(cond + 4 * q) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-                    *(uint4*)(cond + kCondWords + 4 * q) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                    *(uint4*)(cond + kCond + 4 * q) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
                 }
             }
             b = 4 * nquads;
@@ -475,13 +479,25 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t r_
             const uint32_t hi = __ballot_sync(kFull, d < cm.c2);
             if (lane == 0) {
                 cond[b] = lo;
-                cond[kCondWords + b] = hi;
+                cond[kCond + b] = hi;
             }
         }
         __syncwarp();
-        if (act) {
-            if (TRIM) word_update<Word>(a, c, r, y, z, lk, cond, loff, dEsum);
-            else word_compute<Word>(a, c, win, lk, cond, loff, dEsum);
+        if constexpr (WPT == 1) {
+            if (act) {
+                if (TRIM) word_update<Word>(a, c, r, y, z, lk, cond, loff, dEsum);
+                else word_compute<Word>(a, c, win, lk, cond, loff, dEsum);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < WPT; ++q) {
+                const int wi = lane + 32 * q;  // word of the group: row wi / W, word wi % W
+                if (wi < nrows * W) {
+                    const int jq = wi / W, kq = wi - jq * W;
+                    const int rq = (int)g0 + jq;
+                    word_update<Word>(a, c, rq, rq % L, rq / L, kq, cond, jq * half + kq * w, dEsum, kCond);
+                }
+            }
         }
         __syncwarp();
         r += G;

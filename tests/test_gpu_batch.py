@@ -115,7 +115,7 @@ def test_batch_rejects_bad_arguments(isg):
 @pytest.mark.parametrize("kind", ["mt19937", "minstd", "parisi_rapuano"])
 def test_every_execution_configuration_gives_identical_states(isg, kind):
     """Layout and tuning invariance: each candidate the autotuner may pick (CTA
-    shape, streams per bundle, generator-state placement) sweeps the same mixed
+    shape, streams per bundle, generator-state placement, words per lane) sweeps the same mixed
     batch to bit-identical states (energies and hashes of every replica), also
     when the configuration changes between groups of sweeps."""
     from paper_1411_0127_gb300 import autotune
@@ -128,7 +128,7 @@ def test_every_execution_configuration_gives_identical_states(isg, kind):
     for cand in cands:
         b = isg.Batch(L, J, S, B, kind)
         b.set_config(*cand)
-        assert b.get_config() == (cand[0], cand[1], cand[2])
+        assert b.get_config() == tuple(cand)
         b.run(6, 3)
         E, H = b.tracked()
         assert np.array_equal(E, E0) and np.array_equal(H, H0), cand
@@ -167,8 +167,8 @@ def test_autotuner_picks_a_candidate_and_caches_it(isg, tmp_path):
 def test_batch_config_rejects_bad_values(isg):
     L, J, S, B = mixed()
     b = isg.Batch(L[:2], J[:2], S[:4], B[:2], "minstd")
-    for bad in [(4, 0, 1), (-1, 0, 1), (2, 17, 1), (0, 33, 1), (0, 8, 2)]:
+    for bad in [(4, 0, 1, 1), (-1, 0, 1, 1), (2, 17, 1, 1), (0, 33, 1, 1), (0, 8, 2, 1), (0, 8, 1, 3), (0, 8, 1, 0)]:
         with pytest.raises(isg.IsgError):
             b.set_config(*bad)
-    assert b.get_config() == (0, 32, 1)
+    assert b.get_config() == (0, 32, 1, 1)
     b.close()
