@@ -122,9 +122,9 @@ __device__ __forceinline__ void mt_make_room(uint32_t* B, int& iA, int need, int
 // Four 32-draw blocks (128 draws) at once.  Block j reads x_{k+32j+l+397},
 // which was appended 227 - 32j - l >= 100 draws before this step, so every
 // read of the step can precede every write (one warp barrier between).
-template <int SLACK>
+template <int SLACK, bool ROOM = true>
 __device__ __forceinline__ void mt_quad(uint32_t* B, int& iA, uint32_t d[4], const MtMul& k, int lane) {
-    mt_make_room<SLACK>(B, iA, 128, lane);
+    if (ROOM) mt_make_room<SLACK>(B, iA, 128, lane);
     uint32_t a[4], b[4], m[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -342,38 +342,59 @@ __device__ __forceinline__ bool level_lo(uint32_t d, const Cmp& a) {
     return (d < a.c1) ^ (d < a.c2) ^ (d < a.c3);
 }
 
-// The two ballots of N consecutive 32-draw blocks.  A draw below cmp2 has
-// probability exp(-8 beta) (1.4e-4 at T = 0.9), so with TRIM the warp first asks
-// whether any of its 32 N draws is below cmp2.  If none is, none is below cmp3
-// either, every level is 0 or 1, and one comparison per draw gives it exactly.
-// The extra vote lengthens the dependency chain of a step, so kernels whose
-// warps are too few to hide latency are built without TRIM.
-template <int N, bool TRIM>
+// The two ballots of N consecutive 32-draw blocks.
+template <int N>
 __device__ __forceinline__ void level_ballots(const uint32_t (&d)[N], const Cmp& a, uint32_t (&lo)[N],
                                               uint32_t (&hi)[N]) {
-    uint32_t dmin = d[0];
 #pragma unroll
-    for (int j = 1; j < N; ++j) dmin = min(dmin, d[j]);
-    if (!TRIM || __any_sync(kFull, dmin < a.c2)) {
+    for (int j = 0; j < N; ++j) {
+        lo[j] = __ballot_sync(kFull, level_lo(d[j], a));
+        hi[j] = __ballot_sync(kFull, d[j] < a.c2);
+    }
+}
+
+// The throughput form of the ballots of a quad of blocks.  A draw below cmp2 has
+// probability exp(-8 beta) (1.4e-4 at T = 0.9), so the warp first asks whether
+// any of its 128 draws is below cmp2.  If none is, none is below cmp3 either,
+// every level is 0 or 1, one comparison per draw gives it exactly and the hi
+// ballots are all zero.  The extra vote lengthens the dependency chain of a
+// step, so kernels whose warps are too few to hide latency do without it.
+// Lane 0 stores the four lo ballots to lo_dst and, only when the hi ballots are
+// taken, the four hi ballots to hi_dst; returns whether it stored them.  The hi
+// stream is otherwise left as it is (kept all zero by the caller).
+__device__ __forceinline__ bool quad_ballots(const uint32_t (&d)[4], const Cmp& a, uint32_t* lo_dst,
+                                             uint32_t* hi_dst, int lane) {
+    const uint32_t dmin = min(min(d[0], d[1]), min(d[2], d[3]));
+    if (__any_sync(kFull, dmin < a.c2)) {
+        uint32_t lo[4], hi[4];
 #pragma unroll
-        for (int j = 0; j < N; ++j) {
+        for (int j = 0; j < 4; ++j) {
             lo[j] = __ballot_sync(kFull, level_lo(d[j], a));
             hi[j] = __ballot_sync(kFull, d[j] < a.c2);
         }
-    } else {
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            lo[j] = __ballot_sync(kFull, d[j] < a.c1);
-            hi[j] = 0u;
+        if (lane == 0) {
+            *(uint4*)lo_dst = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+            *(uint4*)hi_dst = make_uint4(hi[0], hi[1], hi[2], hi[3]);
         }
+        return true;
     }
+    uint32_t lo[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) lo[j] = __ballot_sync(kFull, d[j] < a.c1);
+    if (lane == 0) *(uint4*)lo_dst = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    return false;
+}
+
+// Zeroes the hi bit stream of the condition buffer (n words).
+__device__ __forceinline__ void clear_hi(uint32_t* hi, int n, int lane) {
+    for (int j = lane; j < n; j += 32) hi[j] = 0u;
 }
 
 // One pass of colour c over rows [r_begin, r_end) of a stream (all of its rows,
 // or a segment that starts at a row group); the generator state, positioned at
 // the first of these rows, is in B / st.  SLACK is the free space of the
 // MT19937 window (see mt_window); TRIM selects the throughput form of the draw
-// phase (level_ballots; MINSTD four blocks per step) over the latency one
+// phase (quad_ballots; MINSTD four blocks per step) over the latency one
 // (MINSTD two blocks per step, MT19937 seven, the word-update loads issued
 // before the draws).  WPT is the number of words of a row group each lane
 // updates: a group is WPT * 32 / W rows, and cond holds two bit streams of
@@ -392,6 +413,11 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t r_
     const int loff = lj * half + lk * w;
     int r = (int)r_begin + lj;
     int y = r % L, z = r / L;
+    bool hiset = false;  // TRIM: the hi stream holds a nonzero word
+    if (TRIM) {
+        clear_hi(cond + kCond, kCond, lane);
+        __syncwarp();
+    }
     for (int64_t g0 = r_begin; g0 < r_end; g0 += G) {
         const int nrows = (int)((r_end - g0) < G ? (r_end - g0) : G);
         const int D = nrows * half;
@@ -408,7 +434,7 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t r_
             for (int q = 0; q < nsev; ++q) {
                 uint32_t d[7], lo[7], hi[7];
                 mt_seven<SLACK>(B, st.iA, d, k.mul, lane);
-                level_ballots<7, false>(d, cm, lo, hi);
+                level_ballots<7>(d, cm, lo, hi);
                 uint32_t l = lo[0], h = hi[0];
 #pragma unroll
                 for (int j = 1; j < 7; ++j)
@@ -428,7 +454,7 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t r_
                 uint32_t d[2] = {st.xA, st.xB}, lo[2], hi[2];
                 st.xA = minstd_mulmod(st.xA, k.a64);
                 st.xB = minstd_mulmod(st.xB, k.a64);
-                level_ballots<2, false>(d, cm, lo, hi);
+                level_ballots<2>(d, cm, lo, hi);
                 if (lane == 0) {
                     *(uint2*)(cond + 2 * q) = make_uint2(lo[0], lo[1]);
                     *(uint2*)(cond + kCond + 2 * q) = make_uint2(hi[0], hi[1]);
@@ -436,26 +462,42 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t r_
             }
             b = 2 * npairs;
         } else {
+            // With TRIM the hi stream is kept all zero between groups and a quad
+            // whose hi ballots were skipped stores nothing there.  MT19937 checks
+            // its window once per run of quads that fit.
             const int nquads = D >> 7;
-            for (int q = 0; q < nquads; ++q) {
-                uint32_t d[4], lo[4], hi[4];
+            for (int q = 0; q < nquads;) {
+                int qe = nquads;
                 if (kMT) {
-                    mt_quad<SLACK>(B, st.iA, d, k.mul, lane);
-                } else if (KIND == ISG_RNG_PARISI_RAPUANO) {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) d[j] = pr_warp_step(st.xA, st.xB, lane, 32);
-                } else {
-                    d[0] = st.xA;
-                    d[1] = st.xB;
-                    d[2] = minstd_mulmod(st.xA, k.a64);
-                    d[3] = minstd_mulmod(st.xB, k.a64);
-                    st.xA = minstd_mulmod(d[2], k.a64);
-                    st.xB = minstd_mulmod(d[3], k.a64);
+                    mt_make_room<SLACK>(B, st.iA, 128, lane);
+                    const int fit = q + ((mt_window(SLACK) - kMtN - st.iA) >> 7);
+                    qe = fit < nquads ? fit : nquads;
                 }
-                level_ballots<4, TRIM>(d, cm, lo, hi);
-                if (lane == 0) {
-                    *(uint4*)(cond + 4 * q) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-                    *(uint4*)(cond + kCond + 4 * q) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                for (; q < qe; ++q) {
+                    uint32_t d[4];
+                    if (kMT) {
+                        mt_quad<SLACK, false>(B, st.iA, d, k.mul, lane);
+                    } else if (KIND == ISG_RNG_PARISI_RAPUANO) {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) d[j] = pr_warp_step(st.xA, st.xB, lane, 32);
+                    } else {
+                        d[0] = st.xA;
+                        d[1] = st.xB;
+                        d[2] = minstd_mulmod(st.xA, k.a64);
+                        d[3] = minstd_mulmod(st.xB, k.a64);
+                        st.xA = minstd_mulmod(d[2], k.a64);
+                        st.xB = minstd_mulmod(d[3], k.a64);
+                    }
+                    if constexpr (TRIM) {
+                        if (quad_ballots(d, cm, cond + 4 * q, cond + kCond + 4 * q, lane)) hiset = true;
+                    } else {
+                        uint32_t lo[4], hi[4];
+                        level_ballots<4>(d, cm, lo, hi);
+                        if (lane == 0) {
+                            *(uint4*)(cond + 4 * q) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                            *(uint4*)(cond + kCond + 4 * q) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                        }
+                    }
                 }
             }
             b = 4 * nquads;
@@ -477,6 +519,7 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t r_
             }
             const uint32_t lo = __ballot_sync(kFull, level_lo(d, cm));
             const uint32_t hi = __ballot_sync(kFull, d < cm.c2);
+            hiset |= hi != 0u;
             if (lane == 0) {
                 cond[b] = lo;
                 cond[kCond + b] = hi;
@@ -500,6 +543,11 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t r_
             }
         }
         __syncwarp();
+        if (TRIM && hiset) {
+            clear_hi(cond + kCond, kCond, lane);
+            hiset = false;
+            __syncwarp();
+        }
         r += G;
         y += G;
         while (y >= L) {
