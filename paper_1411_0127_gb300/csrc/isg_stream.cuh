@@ -359,29 +359,53 @@ __device__ __forceinline__ void level_ballots(const uint32_t (&d)[N], const Cmp&
 // every level is 0 or 1, one comparison per draw gives it exactly and the hi
 // ballots are all zero.  The extra vote lengthens the dependency chain of a
 // step, so kernels whose warps are too few to hide latency do without it.
-// Lane 0 stores the four lo ballots to lo_dst and, only when the hi ballots are
-// taken, the four hi ballots to hi_dst; returns whether it stored them.  The hi
-// stream is otherwise left as it is (kept all zero by the caller).
-__device__ __forceinline__ bool quad_ballots(const uint32_t (&d)[4], const Cmp& a, uint32_t* lo_dst,
-                                             uint32_t* hi_dst, int lane) {
+// 16-byte shared-memory store by lane 0 alone, as one predicated instruction
+// (no divergent branch around it); `addr` is a shared-window address.
+__device__ __forceinline__ void st_shared_lane0(uint32_t addr, uint32_t x, uint32_t y, uint32_t z, uint32_t w,
+                                                int lane) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.eq.s32 p, %5, 0;\n\t@p st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n\t}"
+        :
+        : "r"(addr), "r"(x), "r"(y), "r"(z), "r"(w), "r"(lane)
+        : "memory");
+}
+
+// Four ballot words stored by lane 0: with PST as one predicated instruction
+// (faster for MT19937, whose step has more shared-memory traffic), otherwise
+// under a branch (faster for the register generators).  `p` and `s` are the
+// generic and shared-window addresses of the same words.
+template <bool PST>
+__device__ __forceinline__ void store4_lane0(uint32_t* p, uint32_t s, const uint32_t (&v)[4], int lane) {
+    if constexpr (PST) {
+        st_shared_lane0(s, v[0], v[1], v[2], v[3], lane);
+    } else {
+        if (lane == 0) *(uint4*)p = make_uint4(v[0], v[1], v[2], v[3]);
+    }
+}
+
+// Lane 0 stores the four lo ballots at lo and, only when the hi ballots are
+// taken, the four hi ballots at hi (generic pointers, with lo_s and hi_s their
+// shared-window addresses); returns whether it stored them.  The hi stream is
+// otherwise left as it is (kept all zero by the caller).
+template <bool PST>
+__device__ __forceinline__ bool quad_ballots(const uint32_t (&d)[4], const Cmp& a, uint32_t* lo, uint32_t* hi,
+                                             uint32_t lo_s, uint32_t hi_s, int lane) {
     const uint32_t dmin = min(min(d[0], d[1]), min(d[2], d[3]));
     if (__any_sync(kFull, dmin < a.c2)) {
-        uint32_t lo[4], hi[4];
+        uint32_t l[4], h[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            lo[j] = __ballot_sync(kFull, level_lo(d[j], a));
-            hi[j] = __ballot_sync(kFull, d[j] < a.c2);
+            l[j] = __ballot_sync(kFull, level_lo(d[j], a));
+            h[j] = __ballot_sync(kFull, d[j] < a.c2);
         }
-        if (lane == 0) {
-            *(uint4*)lo_dst = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-            *(uint4*)hi_dst = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        }
+        store4_lane0<PST>(lo, lo_s, l, lane);
+        store4_lane0<PST>(hi, hi_s, h, lane);
         return true;
     }
-    uint32_t lo[4];
+    uint32_t l[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) lo[j] = __ballot_sync(kFull, d[j] < a.c1);
-    if (lane == 0) *(uint4*)lo_dst = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    for (int j = 0; j < 4; ++j) l[j] = __ballot_sync(kFull, d[j] < a.c1);
+    store4_lane0<PST>(lo, lo_s, l, lane);
     return false;
 }
 
@@ -414,6 +438,7 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t r_
     int r = (int)r_begin + lj;
     int y = r % L, z = r / L;
     bool hiset = false;  // TRIM: the hi stream holds a nonzero word
+    const uint32_t cond_s = (uint32_t)__cvta_generic_to_shared(cond);
     if (TRIM) {
         clear_hi(cond + kCond, kCond, lane);
         __syncwarp();
@@ -489,7 +514,9 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t r_
                         st.xB = minstd_mulmod(d[3], k.a64);
                     }
                     if constexpr (TRIM) {
-                        if (quad_ballots(d, cm, cond + 4 * q, cond + kCond + 4 * q, lane)) hiset = true;
+                        if (quad_ballots<kMT>(d, cm, cond + 4 * q, cond + kCond + 4 * q, cond_s + 16 * q,
+                                              cond_s + 4 * kCond + 16 * q, lane))
+                            hiset = true;
                     } else {
                         uint32_t lo[4], hi[4];
                         level_ballots<4>(d, cm, lo, hi);
