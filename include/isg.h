@@ -214,9 +214,14 @@ int isg_batch_member(isg_batch *b, int i, isg_sim **out);
 
 /* Enqueue `sweeps` sweeps of every replica (async).  The work runs as persistent
  * launches of group_sweeps sweeps (<= 0 picks 64): the CTAs of the execution
- * configuration (isg_batch_set_config) take bundle after bundle; the group
+ * configuration (isg_batch_set_config) take task after task; the group
  * launch is captured once into a CUDA graph and replayed; a remainder of
- * sweeps % group_sweeps is launched directly. */
+ * sweeps % group_sweeps is launched directly.  A task is a bundle of RNG
+ * streams for all of the launch's sweeps or, for a bundle longer than a sixth
+ * of the average work per CTA, one of up to 8 consecutive parts of them; a
+ * part waits (bounded, about 4 s) for the previous part, run by another CTA.
+ * If such a wait ever gives up, the next isg_batch_measure / isg_batch_tracked
+ * returns ISG_ERR_TIMEOUT once (the bundle's lattices then missed sweeps). */
 int isg_batch_run(isg_batch *b, int64_t sweeps, int group_sweeps, void *cuda_stream);
 
 /* Energies from scratch of the 2n replicas (E[2s], E[2s+1]) and overlaps
@@ -353,6 +358,12 @@ int isg_stencil_decisions(const uint16_t *code, const uint32_t *draw, int64_t n,
 /* First n draws of stream t of the handle's generator, from its current
  * position, without advancing it (sync); host_out gets the 32-bit draws. */
 int isg_peek_draws(const isg_sim *h, int64_t t, int64_t n, uint32_t *host_out);
+
+/* Make the last task of the batch's launches wait for itself, a flag that
+ * nothing sets, so that its bounded wait runs out (about 4 s per launch) and
+ * the error path can be tested.  The next isg_batch_set_config restores the
+ * plan.  ISG_ERR_STATE if the batch has fewer than two tasks. */
+int isg_batch_test_stall(isg_batch *b);
 
 #ifdef __cplusplus
 }

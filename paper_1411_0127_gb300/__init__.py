@@ -52,6 +52,7 @@ SIGNATURES = {
     "isg_load": (_i32, [_vp, _sz, _PP]),
     "isg_stencil_decisions": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp]),
     "isg_peek_draws": (_i32, [_vp, _i64, _i64, _vp]),
+    "isg_batch_test_stall": (_i32, [_vp]),
     "isg_energy_static_scratch": (_i32, [_vp, _vp, _vp]),
     "isg_batch_create": (_i32, [_i32, _vp, _vp, _vp, _vp, _i32, _PP]),
     "isg_batch_destroy": (None, [_vp]),

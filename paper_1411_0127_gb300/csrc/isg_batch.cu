@@ -23,6 +23,7 @@
 // site to stream and draw), which the tests check against isg_sweep and the
 // CPU oracle.
 #include <algorithm>
+#include <cmath>
 #include <type_traits>
 #include <cstring>
 #include <new>
@@ -38,7 +39,8 @@ struct isg_batch {
     isg::FlipArgs* d_reps = nullptr;    // per-lattice descriptors
     int2* d_entries = nullptr;          // (lattice, stream) grouped by bundle
     int* d_boff = nullptr;              // bundle offsets into d_entries
-    unsigned* d_ctr = nullptr;          // [0] next bundle, [1] CTAs done
+    unsigned* d_ctr = nullptr;          // [0] next task, [1] CTAs done, [2] dependency-wait error
+    isg::BundleTasks tasks;             // launch order of the bundles, long ones split in two
     int nbundles = 0;
     int64_t attempts_per_sweep = 0;
     isg::BundleConfig cfg;              // execution configuration (isg_batch_set_config)
@@ -60,8 +62,15 @@ struct BatchArgs {
     int nbundles;
     int sweeps;
     int resident;         // keep the generator state of bundles that fit in the CTA for the whole launch
-    unsigned* ctr;
+    unsigned* ctr;        // [0] next task, [1] CTAs done, [2] sticky error: a dependency wait gave up
+    const int4* tasks;    // NULL: task i is bundle i, all its sweeps; else see BundleTasks
+    int ntasks;
+    unsigned* done;       // per task: its sweeps are done (first halves only); zeroed at the end of a launch
 };
+
+// Iterations of the wait for a first half (each about 0.25 us of sleep): seconds
+// beyond any real wait, after which the kernel sets ctr[2] and skips the task.
+constexpr int kDepWaitLimit = 1 << 24;
 
 // CTA shapes of the bundle kernel (warps per CTA, CTAs per SM); see BundleConfig.
 struct BundleShape {
@@ -73,19 +82,42 @@ template <int KIND, int WARPS, int PER_SM, int WPT>
 __global__ void __launch_bounds__(WARPS * 32, PER_SM) batch_kernel(BatchArgs b, StreamConst k) {
     constexpr int kBatchWarps = WARPS;
     extern __shared__ uint32_t smem[];
-    __shared__ int s_bundle;
+    __shared__ int s_task, s_ok;
     constexpr int kRing = KIND == ISG_RNG_MT19937 ? mt_window(kBatchSlack) : 0;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint32_t* ring = smem + wid * (kRing + 2 * WPT * kCondWords);
     uint32_t* cond = ring + kRing;
+    const int ntasks = b.tasks ? b.ntasks : b.nbundles;
     for (;;) {
-        if (threadIdx.x == 0) s_bundle = (int)atomicAdd(&b.ctr[0], 1u);
+        if (threadIdx.x == 0) s_task = (int)atomicAdd(&b.ctr[0], 1u);
         __syncthreads();
-        const int bid = s_bundle;
+        const int tid = s_task;
         __syncthreads();
-        if (bid >= b.nbundles) break;
+        if (tid >= ntasks) break;
+        const int4 tk = b.tasks ? b.tasks[tid] : make_int4(tid, 0, -1, 0);
+        const int bid = tk.x;
+        int sweeps = b.bsweeps ? b.bsweeps[bid] : b.sweeps;
+        if (tk.y > 0) sweeps = sweeps * tk.y / tk.w - sweeps * (tk.y - 1) / tk.w;  // part y of w
+        if (tk.z >= 0) {
+            // the previous part of this bundle's sweeps is task tk.z, taken
+            // earlier by a running CTA: wait (bounded) until it has finished
+            if (threadIdx.x == 0) {
+                int ok = 0;
+                for (int it = 0; it < kDepWaitLimit; ++it) {
+                    if (*(volatile const unsigned*)(b.done + tk.z) != 0u) {
+                        ok = 1;
+                        break;
+                    }
+                    __nanosleep(256);
+                }
+                __threadfence();
+                if (!ok) atomicExch(&b.ctr[2], 1u);
+                s_ok = ok;
+            }
+            __syncthreads();
+            if (!s_ok) continue;
+        }
         const int e0 = b.boff[bid], n = b.boff[bid + 1] - e0;
-        const int sweeps = b.bsweeps ? b.bsweeps[bid] : b.sweeps;
         const bool resident = b.resident && n <= kBatchWarps;
         StreamRegs st;
         if (resident && wid < n) {
@@ -95,14 +127,27 @@ __global__ void __launch_bounds__(WARPS * 32, PER_SM) batch_kernel(BatchArgs b, 
         for (int pass = 0; pass < 2 * sweeps; ++pass) {
             for (int j = wid; j < n; j += kBatchWarps) {
                 const int2 e = b.entries[e0 + j];
-                const FlipArgs& a = b.reps[e.x];
-                if (!resident) load_stream<KIND>(a, e.y, ring, st, k, lane);
+                const FlipArgs& g = b.reps[e.x];
+                if (!resident) load_stream<KIND>(g, e.y, ring, st, k, lane);
+                // The fields the pass reads, held in registers: read through the
+                // descriptor in global memory they would be re-read after every
+                // store to the spin planes.
+                FlipArgs a;
+                a.planes = g.planes;
+                a.plane_bytes = g.plane_bytes;
+                a.L = g.L;
+                a.half = g.half;
+                a.W = g.W;
+                a.nt = g.nt;
+                a.cmp1 = g.cmp1;
+                a.cmp2 = g.cmp2;
+                a.cmp3 = g.cmp3;
                 int dE = 0;
-                const int64_t rb = (int64_t)e.y * a.R, re = rb + a.R < a.rows ? rb + a.R : a.rows;
+                const int64_t rb = (int64_t)e.y * g.R, re = rb + g.R < g.rows ? rb + g.R : g.rows;
                 stream_pass<uint32_t, KIND, kBatchSlack, true, WPT>(a, pass & 1, rb, re, ring, cond, st, k, lane, dE);
-                if (!resident) store_stream<KIND>(a, e.y, ring, st, lane);
+                if (!resident) store_stream<KIND>(g, e.y, ring, st, lane);
                 for (int sh = 16; sh; sh >>= 1) dE += __shfl_xor_sync(kFull, dE, sh);
-                if (lane == 0 && dE != 0) atomicAdd((unsigned long long*)a.dE, (unsigned long long)(long long)dE);
+                if (lane == 0 && dE != 0) atomicAdd((unsigned long long*)g.dE, (unsigned long long)(long long)dE);
             }
             __syncthreads();
         }
@@ -110,12 +155,20 @@ __global__ void __launch_bounds__(WARPS * 32, PER_SM) batch_kernel(BatchArgs b, 
             const int2 e = b.entries[e0 + wid];
             store_stream<KIND>(b.reps[e.x], e.y, ring, st, lane);
         }
+        if (tk.y > 0 && tk.y < tk.w) {  // publish this part to the one that waits for it
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicExch(b.done + tid, 1u);
+            }
+        }
     }
-    // the last CTA to leave returns both counters to zero for the next launch
+    // the last CTA to leave returns the counters and flags to zero for the next launch
     if (threadIdx.x == 0) {
         __threadfence();
         const unsigned done = atomicAdd(&b.ctr[1], 1u);
         if (done == gridDim.x - 1) {
+            for (int t = 0; b.tasks && t < b.ntasks; ++t) b.done[t] = 0u;
             atomicExch(&b.ctr[0], 0u);
             atomicExch(&b.ctr[1], 0u);
             __threadfence();
@@ -161,7 +214,7 @@ cudaError_t prepare_bundle_kernel(int kind, const BundleConfig& cfg) {
 
 cudaError_t launch_bundle_kernel(int kind, const BundleConfig& cfg, const FlipArgs* reps, const int2* entries,
                                  const int* boff, const int* bsweeps, int nbundles, int sweeps, unsigned* ctr,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, const BundleTasks* tasks) {
     if (nbundles <= 0) return cudaSuccess;
     BatchArgs a;
     a.reps = reps;
@@ -172,6 +225,9 @@ cudaError_t launch_bundle_kernel(int kind, const BundleConfig& cfg, const FlipAr
     a.sweeps = sweeps;
     a.resident = cfg.resident;
     a.ctr = ctr;
+    a.tasks = tasks ? tasks->d_tasks : nullptr;
+    a.ntasks = tasks ? tasks->ntasks : nbundles;
+    a.done = tasks ? tasks->d_done : nullptr;
     const StreamConst k = stream_const();
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -181,7 +237,7 @@ cudaError_t launch_bundle_kernel(int kind, const BundleConfig& cfg, const FlipAr
             return with_wpt(cfg.wpt, [&](auto wc) {
                 constexpr BundleShape sh = kBundleShapes[decltype(sc)::value];
                 constexpr int wpt = decltype(wc)::value;
-                const int grid = std::max(1, std::min(sms * sh.per_sm, nbundles));
+                const int grid = std::max(1, std::min(sms * sh.per_sm, a.ntasks));
                 batch_kernel<decltype(kc)::value, sh.warps, sh.per_sm, wpt>
                     <<<grid, sh.warps * 32, batch_smem(kind, sh.warps, wpt), s>>>(a, k);
                 return cudaGetLastError();
@@ -248,7 +304,51 @@ void plan_bundles(const std::vector<isg_sim*>& reps, std::vector<int2>& entries,
 
 static cudaError_t batch_launch(isg_batch* b, int sweeps, cudaStream_t s) {
     return launch_bundle_kernel(b->kind, b->cfg, b->d_reps, b->d_entries, b->d_boff, nullptr, b->nbundles, sweeps,
-                                b->d_ctr, s);
+                                b->d_ctr, s, &b->tasks);
+}
+
+// Task order of a launch.  A persistent CTA takes whole bundles, so a bundle far
+// longer than the average work per CTA decides when the launch ends (e.g. 162
+// lattices of L = 192, one bundle each, on 152 CTAs: ten CTAs run two).  A
+// bundle with more than kSplitDiv-th of that average is split into up to
+// kSplitMax consecutive parts of its sweeps: all first parts go first, then all
+// second parts in the same order (each waiting for its own previous part, which
+// a running CTA took earlier), and so on, then the other bundles, longest first.
+constexpr int kSplitMax = 8, kSplitDiv = 6;
+static std::vector<int4> split_tasks(const isg_batch* b, const std::vector<int2>& entries,
+                                     const std::vector<int>& boff, int ctas) {
+    const int nb = (int)boff.size() - 1, warps = bundle_warps(b->cfg);
+    std::vector<double> work(nb, 0.0);
+    double total = 0.0;
+    for (int i = 0; i < nb; ++i) {
+        double per_round = 0.0;
+        for (int j = boff[i]; j < boff[i + 1]; ++j) {
+            const isg_sim* h = b->reps[entries[j].x];
+            per_round = std::max(per_round, (double)h->R * h->half);
+        }
+        const int n = boff[i + 1] - boff[i];
+        work[i] = (double)((n + warps - 1) / warps) * per_round;
+        total += work[i];
+    }
+    const double piece = total / std::max(1, ctas) / kSplitDiv;
+    std::vector<int> parts(nb, 1);
+    int maxparts = 1;
+    for (int i = 0; i < nb; ++i) {
+        parts[i] = (int)std::min<double>(kSplitMax, std::ceil(work[i] / piece));
+        if (parts[i] < 1) parts[i] = 1;
+        maxparts = std::max(maxparts, parts[i]);
+    }
+    std::vector<int4> out;
+    std::vector<int> prev(nb, -1);
+    for (int p = 1; p <= maxparts; ++p)
+        for (int i = 0; i < nb; ++i)
+            if (parts[i] > 1 && p <= parts[i]) {
+                out.push_back(make_int4(i, p, prev[i], parts[i]));
+                prev[i] = (int)out.size() - 1;
+            }
+    for (int i = 0; i < nb; ++i)
+        if (parts[i] == 1) out.push_back(make_int4(i, 0, -1, 1));
+    return out;
 }
 
 // Bundles for the configuration's capacity, uploaded (the entries keep their
@@ -269,8 +369,24 @@ static int batch_plan(isg_batch* b) {
         return ISG_ERR_NOMEM;
     }
     b->nbundles = (int)boff.size() - 1;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const std::vector<int4> tasks = split_tasks(b, entries, boff, sms * kBundleShapes[b->cfg.shape].per_sm);
+    dev_free(h0, b->tasks.d_tasks);
+    dev_free(h0, b->tasks.d_done);
+    b->tasks.ntasks = (int)tasks.size();
+    b->tasks.d_tasks = (int4*)dev_alloc(h0, tasks.size() * sizeof(int4));
+    b->tasks.d_done = (unsigned*)dev_alloc(h0, tasks.size() * sizeof(unsigned));
+    if (!b->tasks.d_tasks || !b->tasks.d_done) {
+        set_error("isg_batch: device allocation failed");
+        return ISG_ERR_NOMEM;
+    }
     cudaError_t e = cudaMemcpy(b->d_entries, entries.data(), entries.size() * sizeof(int2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_boff, boff.data(), boff.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->tasks.d_tasks, tasks.data(), tasks.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(b->tasks.d_done, 0, tasks.size() * sizeof(unsigned));
     if (e == cudaSuccess) e = prepare_bundle_kernel(b->kind, b->cfg);
     return e == cudaSuccess ? ISG_OK : cuda_fail(e, "isg_batch: bundle plan");
 }
@@ -285,6 +401,8 @@ static void batch_free(isg_batch* b) {
         dev_free(b->reps[0], b->d_entries);
         dev_free(b->reps[0], b->d_boff);
         dev_free(b->reps[0], b->d_ctr);
+        dev_free(b->reps[0], b->tasks.d_tasks);
+        dev_free(b->reps[0], b->tasks.d_done);
     }
     for (isg_sim* h : b->reps) destroy_sim(h);
     delete b;
@@ -327,7 +445,7 @@ int isg_batch_create(int n, const int* L, const uint64_t* seed_J, const uint64_t
     for (int r = 0; r < 2 * n; ++r) desc[r] = make_flip_args(b->reps[r], 0);
     isg_sim* h0 = b->reps[0];
     b->d_reps = (FlipArgs*)dev_alloc(h0, desc.size() * sizeof(FlipArgs));
-    b->d_ctr = (unsigned*)dev_alloc(h0, 2 * sizeof(unsigned));
+    b->d_ctr = (unsigned*)dev_alloc(h0, 3 * sizeof(unsigned));
     if (!b->d_reps || !b->d_ctr) {
         batch_free(b);
         set_error("isg_batch_create: device allocation failed");
@@ -338,7 +456,7 @@ int isg_batch_create(int n, const int* L, const uint64_t* seed_J, const uint64_t
         return rc;
     }
     cudaError_t e = cudaMemcpy(b->d_reps, desc.data(), desc.size() * sizeof(FlipArgs), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(b->d_ctr, 0, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(b->d_ctr, 0, 3 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         batch_free(b);
@@ -393,6 +511,27 @@ int isg_batch_get_config(const isg_batch* b, int* shape, int* capacity, int* res
     return ISG_OK;
 }
 
+int isg_batch_test_stall(isg_batch* b) {
+    if (!b) { set_error("isg_batch_test_stall: NULL batch"); return ISG_ERR_ARG; }
+    const int n = b->tasks.ntasks;
+    if (n < 2) { set_error("isg_batch_test_stall: fewer than two tasks"); return ISG_ERR_STATE; }
+    int4 t;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&t, b->tasks.d_tasks + (n - 1), sizeof(int4), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "isg_batch_test_stall");
+    t.z = n - 1;  // its own flag: a part-0 or last part never sets it
+    if (t.y == 0) {
+        t.y = 1;
+        t.w = 1;
+    }
+    e = cudaMemcpy(b->tasks.d_tasks + (n - 1), &t, sizeof(int4), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "isg_batch_test_stall");
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    b->graph_group = 0;
+    return ISG_OK;
+}
+
 int isg_batch_member(isg_batch* b, int i, isg_sim** out) {
     if (!b || !out || i < 0 || i >= 2 * b->n) { set_error("isg_batch_member: bad argument"); return ISG_ERR_ARG; }
     *out = b->reps[i];
@@ -429,8 +568,24 @@ int isg_batch_run(isg_batch* b, int64_t sweeps, int group_sweeps, void* cuda_str
     return ISG_OK;
 }
 
+// ISG_ERR_TIMEOUT (once) if a launch gave up waiting for the first half of a
+// split bundle: that bundle's lattices then missed sweeps.
+static int batch_check(isg_batch* b, cudaStream_t s) {
+    unsigned err = 0;
+    cudaError_t e = cudaMemcpyAsync(&err, b->d_ctr + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "isg_batch: error check");
+    if (err) {
+        cudaMemsetAsync(b->d_ctr + 2, 0, sizeof(unsigned), s);
+        set_error("isg_batch: a split bundle's second half gave up waiting for its first half");
+        return ISG_ERR_TIMEOUT;
+    }
+    return ISG_OK;
+}
+
 int isg_batch_measure(isg_batch* b, int64_t* E, int64_t* Q, void* cuda_stream) {
     if (!b) { set_error("isg_batch_measure: NULL batch"); return ISG_ERR_ARG; }
+    if (const int rc = batch_check(b, (cudaStream_t)cuda_stream)) return rc;
     for (int r = 0; E && r < 2 * b->n; ++r) {
         const int rc = isg_energy(b->reps[r], &E[r], cuda_stream);
         if (rc) return rc;
@@ -444,6 +599,7 @@ int isg_batch_measure(isg_batch* b, int64_t* E, int64_t* Q, void* cuda_stream) {
 
 int isg_batch_tracked(isg_batch* b, int64_t* E, uint64_t* H, void* cuda_stream) {
     if (!b) { set_error("isg_batch_tracked: NULL batch"); return ISG_ERR_ARG; }
+    if (const int rc = batch_check(b, (cudaStream_t)cuda_stream)) return rc;
     for (int r = 0; r < 2 * b->n; ++r) {
         if (E) {
             const int rc = isg_tracked_energy(b->reps[r], &E[r]);

@@ -38,15 +38,27 @@ int bundle_warps(const BundleConfig& cfg);
 void plan_bundles(const std::vector<isg_sim*>& reps, std::vector<int2>& entries, std::vector<int>& boff,
                   std::vector<int>* order, int capacity = 32);
 
+// Launch order of the bundles (device arrays): task i is (bundle, part, dep,
+// parts): part 0 = all of the launch's sweeps, else part p of `parts`
+// consecutive shares of them, which waits for task dep (the same bundle's part
+// p - 1; -1 for the first) to finish.
+struct BundleTasks {
+    int4* d_tasks = nullptr;
+    unsigned* d_done = nullptr;  // one flag per task, zero between launches
+    int ntasks = 0;
+};
+
 // One-time attribute set-up of the bundle kernel (large dynamic shared memory).
 cudaError_t prepare_bundle_kernel(int kind, const BundleConfig& cfg);
 
 // Launch the persistent bundle kernel: the shape's CTAs per SM (at most one per
-// bundle) sweep bundle after bundle; bundle b runs bsweeps[b] sweeps (or
-// `sweeps` for all when bsweeps is NULL).  ctr must hold two zeroed words; the
-// kernel returns them to zero when it ends.
+// task) sweep task after task; bundle b runs bsweeps[b] sweeps (or `sweeps` for
+// all when bsweeps is NULL), split as `tasks` says (NULL: one task per bundle,
+// in bundle order).  ctr must hold three zeroed words; the kernel returns the
+// first two, and the task flags, to zero when it ends; ctr[2] becomes 1 if a
+// wait for a first half gave up (that second half is then skipped).
 cudaError_t launch_bundle_kernel(int kind, const BundleConfig& cfg, const FlipArgs* reps, const int2* entries,
                                  const int* boff, const int* bsweeps, int nbundles, int sweeps, unsigned* ctr,
-                                 cudaStream_t s);
+                                 cudaStream_t s, const BundleTasks* tasks = nullptr);
 
 }  // namespace isg

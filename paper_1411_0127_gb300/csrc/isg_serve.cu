@@ -187,10 +187,10 @@ int isg_server_create(size_t hbm_budget_bytes, int quantum_sweeps, int max_activ
     for (int k = 0; k < kKinds && e == cudaSuccess; ++k) {
         e = cudaStreamCreateWithFlags(&s->batch_stream[k], cudaStreamNonBlocking);
         if (e == cudaSuccess) {
-            s->plan[k].ctr = (unsigned*)g_dev_alloc(2 * sizeof(unsigned));
+            s->plan[k].ctr = (unsigned*)g_dev_alloc(3 * sizeof(unsigned));
             if (!s->plan[k].ctr) e = cudaErrorMemoryAllocation;
         }
-        if (e == cudaSuccess) e = cudaMemset(s->plan[k].ctr, 0, 2 * sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaMemset(s->plan[k].ctr, 0, 3 * sizeof(unsigned));
         if (e == cudaSuccess) e = prepare_bundle_kernel(k, BundleConfig{});
     }
     for (int k = 0; k < kWideStreams && e == cudaSuccess; ++k)

@@ -172,3 +172,24 @@ def test_batch_config_rejects_bad_values(isg):
             b.set_config(*bad)
     assert b.get_config() == (0, 32, 1, 1)
     b.close()
+
+
+def test_dependency_wait_gives_up_with_a_status(isg):
+    """Failure detection without a GPU fault: the last task is made to wait for
+    a flag that nothing sets.  Its bounded wait runs out, the launch ends, the
+    next read reports ISG_ERR_TIMEOUT once, and the context stays usable."""
+    L, J, S, B = mixed()
+    b = isg.Batch(L, J, S, B, "minstd")
+    assert b.info()["bundles"] >= 2
+    assert isg.lib().isg_batch_test_stall(b._h) == isg.ISG_OK
+    b.run(1, group_sweeps=1)
+    with pytest.raises(isg.IsgError) as ex:
+        b.tracked()
+    assert ex.value.code == isg.ISG_ERR_TIMEOUT
+    b.tracked()                                   # reported once
+    b.set_config(0, 32, 1, 1)                     # a fresh plan
+    b.run(2, group_sweeps=2)
+    Em, _ = b.measure()
+    Et, _ = b.tracked()
+    assert np.array_equal(Em, Et)                 # every replica's bookkeeping intact
+    b.close()
