@@ -65,6 +65,9 @@ def lib() -> ctypes.CDLL:
             "or_mt19937_outputs": (None, [u32, vp, i64]),
             "or_minstd_outputs": (None, [u32, vp, i64]),
             "or_pr_outputs": (None, [u64, vp, i64]),
+            "or_initial_spin": (i32, [u64, i64]),
+            "or_initial_coupling": (i32, [u64, i64, i32]),
+            "or_stream_word": (u64, [u64, i64]),
             "or_unsatisfied": (i32, [ctypes.c_int8, vp, vp]),
             "or_accept": (i32, [i32, u32, vp]),
             "or_create": (vp, [i32, u64, u64, dbl, i32]),
@@ -133,6 +136,21 @@ def pr_outputs(v: int, n: int) -> np.ndarray:
     out = np.empty(n, dtype=np.uint32)
     lib().or_pr_outputs(v & (2**64 - 1), _ptr(out), n)
     return out
+
+
+def initial_spin(seed_spin: int, i: int) -> int:
+    """Spin of site i as or_create draws it (Eq. (2))."""
+    return int(lib().or_initial_spin(seed_spin & (2**64 - 1), int(i)))
+
+
+def initial_coupling(seed_J: int, i: int, d: int) -> int:
+    """Coupling J[d][i] (bond from site i to its +d neighbour) as or_create draws it."""
+    return int(lib().or_initial_coupling(seed_J & (2**64 - 1), int(i), int(d)))
+
+
+def stream_word(seed_rng: int, t: int) -> int:
+    """64-bit seed word of RNG stream t (see or_stream_word)."""
+    return int(lib().or_stream_word(seed_rng & (2**64 - 1), int(t)))
 
 
 def unsatisfied(s: int, nb, J) -> int:
@@ -224,3 +242,98 @@ class OracleSim:
         J = np.ascontiguousarray(J, dtype=np.int8).reshape(-1)
         assert J.size == 3 * self.N
         lib().or_set_couplings(self._h, _ptr(J))
+
+
+def stream_draws(kind: int, word: int, n: int) -> np.ndarray:
+    """The first n draws of a stream with seed word `word`, as the Metropolis
+    rule compares them (Sec. 4): MT19937 and Parisi-Rapuano outputs as they are,
+    MINSTD states doubled (d = 2x)."""
+    if kind == RNG_MT19937:
+        return mt19937_outputs(word & 0xFFFFFFFF, n)
+    if kind == RNG_PR:
+        return pr_outputs(word, n)
+    return (minstd_outputs(1 + word % (2**31 - 2), n).astype(np.uint64) << 1).astype(np.uint32)
+
+
+class SampledFirstSweep:
+    """The spins after the first sweep from the initial state, one site at a time,
+    for lattices too large to hold (L = 2048 is 34 GB as OracleSim's int8
+    arrays).  It takes the same steps as OracleSim in the order the method fixes:
+    the red pass (colour 0) reads only initial blue spins, the blue pass reads the
+    red spins after the red pass; a site of colour c in row r = y + L z owned by
+    stream t = r // R uses draw number (r - t R) L/2 + x // 2 of that stream's
+    pass of colour c, the blue pass starting after the red pass's rows_t L/2
+    draws (Sec. 1 checkerboard; Sec. 4 rule with u unsatisfied bonds)."""
+
+    def __init__(self, L: int, seed_J: int, seed_spin: int, beta: float, kind: int, seed_rng: int = None):
+        self.L, self.seed_J, self.seed_spin, self.kind = L, seed_J, seed_spin, kind
+        self.seed_rng = seed_spin if seed_rng is None else seed_rng
+        self.R, self.S = rows_per_stream(L), num_streams(L)
+        self.thr = thresholds(beta)
+        self._draws = {}   # (stream, draw number) -> draw
+
+    def _rows(self, t: int) -> int:
+        return min(self.R, self.L * self.L - t * self.R)
+
+    def _tk(self, x: int, y: int, z: int):
+        """(stream, draw number in sweep 1) of the attempt at site (x, y, z)."""
+        L = self.L
+        c = (x + y + z) & 1
+        r = (y % L) + L * (z % L)
+        t = r // self.R
+        return t, (r - t * self.R) * (L // 2) + (x % L) // 2 + c * self._rows(t) * (L // 2)
+
+    def _fetch(self, need: dict):
+        """Generate each stream once, up to the largest draw number asked of it,
+        and keep only the draws asked for."""
+        for t, ks in need.items():
+            d = stream_draws(self.kind, stream_word(self.seed_rng, t), max(ks) + 1)
+            for k in ks:
+                self._draws[(t, k)] = int(d[k])
+
+    def _draw(self, t: int, k: int) -> int:
+        if (t, k) not in self._draws:
+            self._fetch({t: {k}})
+        return self._draws[(t, k)]
+
+    def prefetch(self, sites):
+        """Fetch the draws that after() needs for these sites, one generator run
+        per stream (memory stays at one stream's draws)."""
+        need = {}
+        for x, y, z in sites:
+            updates = [(x, y, z)]
+            if (x + y + z) & 1:
+                updates += [(x + 1, y, z), (x - 1, y, z), (x, y + 1, z), (x, y - 1, z), (x, y, z + 1), (x, y, z - 1)]
+            for u in updates:
+                t, k = self._tk(*u)
+                need.setdefault(t, set()).add(k)
+        self._fetch(need)
+
+    def _i(self, x: int, y: int, z: int) -> int:
+        L = self.L
+        return (x % L) + L * (y % L) + L * L * (z % L)
+
+    def initial(self, x: int, y: int, z: int) -> int:
+        return initial_spin(self.seed_spin, self._i(x, y, z))
+
+    def _update(self, x: int, y: int, z: int, nbspin) -> int:
+        L, sJ = self.L, self.seed_J
+        s = self.initial(x, y, z)
+        nb = [nbspin(x + 1, y, z), nbspin(x - 1, y, z), nbspin(x, y + 1, z),
+              nbspin(x, y - 1, z), nbspin(x, y, z + 1), nbspin(x, y, z - 1)]
+        Jb = [initial_coupling(sJ, self._i(x, y, z), 0), initial_coupling(sJ, self._i(x - 1, y, z), 0),
+              initial_coupling(sJ, self._i(x, y, z), 1), initial_coupling(sJ, self._i(x, y - 1, z), 1),
+              initial_coupling(sJ, self._i(x, y, z), 2), initial_coupling(sJ, self._i(x, y, z - 1), 2)]
+        u = unsatisfied(s, nb, Jb)
+        return -s if accept(u, self._draw(*self._tk(x, y, z)), self.thr) else s
+
+    def red(self, x: int, y: int, z: int) -> int:
+        """Spin of a colour-0 site after the red pass of sweep 1."""
+        return self._update(x, y, z, self.initial)
+
+    def after(self, x: int, y: int, z: int) -> int:
+        """Spin of any site after sweep 1."""
+        if (x + y + z) & 1 == 0:
+            return self.red(x, y, z)
+        return self._update(x, y, z, self.red)
+

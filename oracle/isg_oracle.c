@@ -188,6 +188,22 @@ static void stream_seed(stream_t *st, int kind, uint64_t v)
 }
 
 /* ------------------------------------------------------------------------ */
+int or_initial_spin(uint64_t seed_spin, int64_t i)
+{
+    return (or_splitmix64(seed_spin ^ SALT_SPINS, (uint64_t)i) >> 63) ? -1 : 1;
+}
+
+int or_initial_coupling(uint64_t seed_J, int64_t i, int d)
+{
+    return (or_splitmix64(seed_J ^ SALT_COUPLINGS, 3 * (uint64_t)i + (uint64_t)d) >> 63) ? -1 : 1;
+}
+
+uint64_t or_stream_word(uint64_t seed_rng, int64_t t)
+{
+    return or_splitmix64(seed_rng ^ SALT_STREAMS, (uint64_t)t);
+}
+
+/* ------------------------------------------------------------------------ */
 int or_unsatisfied(int8_t s, const int8_t nb[6], const int8_t J[6])
 {
     int u = 0;
@@ -252,13 +268,10 @@ or_sim *or_create2(int L, uint64_t seed_J, uint64_t seed_spin, uint64_t seed_rng
 
     /* Eq. (2): J = +1 or -1 with probability 1/2 each; random +-1 initial spins. */
     for (int64_t i = 0; i < o->N; ++i) {
-        for (int d = 0; d < 3; ++d)
-            o->J[d * o->N + i] =
-                (or_splitmix64(seed_J ^ SALT_COUPLINGS, 3 * (uint64_t)i + (uint64_t)d) >> 63) ? -1 : 1;
-        o->s[i] = (or_splitmix64(seed_spin ^ SALT_SPINS, (uint64_t)i) >> 63) ? -1 : 1;
+        for (int d = 0; d < 3; ++d) o->J[d * o->N + i] = (int8_t)or_initial_coupling(seed_J, i, d);
+        o->s[i] = (int8_t)or_initial_spin(seed_spin, i);
     }
-    for (int64_t t = 0; t < o->S; ++t)
-        stream_seed(&o->st[t], kind, or_splitmix64(seed_rng ^ SALT_STREAMS, (uint64_t)t));
+    for (int64_t t = 0; t < o->S; ++t) stream_seed(&o->st[t], kind, or_stream_word(seed_rng, t));
     o->E0 = or_energy(o);
     o->dE = 0;
     return o;

@@ -50,6 +50,14 @@ void or_minstd_outputs(uint32_t x0, uint32_t *out, int64_t n);      /* successiv
  * for j < 61, ira[60] |= 1; output n is ira[61+n] ^ ira[n]. */
 void or_pr_outputs(uint64_t v, uint32_t *out, int64_t n);
 
+/* The initial state one site at a time, as or_create draws it (Eq. (2)):
+ * the spin of site i, the coupling J[d][i] (d = 0, 1, 2 for x, y, z), and the
+ * 64-bit seed word v_t of RNG stream t (MT19937 is seeded with the low 32 bits
+ * of v_t, MINSTD with 1 + v_t mod (2^31 - 2), Parisi-Rapuano with v_t). */
+int or_initial_spin(uint64_t seed_spin, int64_t i);
+int or_initial_coupling(uint64_t seed_J, int64_t i, int d);
+uint64_t or_stream_word(uint64_t seed_rng, int64_t t);
+
 /* Number of unsatisfied bonds around a site (0..6); s, nb[k], J[k] are +-1. */
 int or_unsatisfied(int8_t s, const int8_t nb[6], const int8_t J[6]);
 /* Metropolis decision for u unsatisfied bonds and a 32-bit draw d: 1 = flip. */

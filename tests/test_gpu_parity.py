@@ -198,6 +198,48 @@ def test_large_workload_two_sweeps(isg):
 
 
 @pytest.mark.parametrize("kind", KINDS)
+def test_maximum_size_sampled(isg, kind):
+    """L = 2048, the largest lattice the ABI accepts: 8.6e9 spins, 4 GiB of bit
+    planes on the device, 34 GB as OracleSim's int8 arrays (too large to hold).
+    The initial spins and the spins after one sweep at sampled sites (rows at
+    stream boundaries and the lattice's last row, x at both ends and at word
+    boundaries, and random sites) are recomputed one by one by the oracle
+    (SampledFirstSweep); the energy bookkeeping is checked as a property that
+    holds at any size (tracked = from scratch)."""
+    L, beta = 2048, 1 / 0.9
+    g = isg.Sim(L, 1, 2, beta, kind)
+    smp = oracle.SampledFirstSweep(L, 1, 2, beta, isg.RNG_KINDS[kind])
+    R, S = oracle.rows_per_stream(L), oracle.num_streams(L)
+    sites = []
+    for r in (0, R - 1, R, (S // 2) * R, (S - 1) * R - 1, (S - 1) * R, L * L - 1):
+        for x in (0, 1, 2, 63, 64, 65, L // 2 - 1, L // 2, L - 2, L - 1):
+            sites.append((x, r % L, r // L))
+    rng = np.random.default_rng(11)
+    sites += [tuple(int(v) for v in rng.integers(0, L, 3)) for _ in range(300)]
+
+    def spin(bits, x, y, z):
+        i = x + L * y + L * L * z
+        return 1 if (int(bits[i >> 3]) >> (i & 7)) & 1 else -1
+
+    smp.prefetch(sites)
+    bits = g.read_spins_packed()
+    for x, y, z in sites:
+        assert spin(bits, x, y, z) == smp.initial(x, y, z), (x, y, z)
+    g.sweep(1)
+    g.read_spins_packed(out=bits)
+    flips = 0
+    for x, y, z in sites:
+        want = smp.after(x, y, z)
+        assert spin(bits, x, y, z) == want, (x, y, z)
+        flips += want != smp.initial(x, y, z)
+    assert flips > len(sites) // 10
+    E = g.tracked_energy()
+    assert E == g.energy()
+    assert abs(E) <= 3 * L ** 3 and (E - 3 * L ** 3) % 2 == 0
+    g.close()
+
+
+@pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("L", [432, 512])
 def test_throughput_form_lattices(isg, L, kind):
     """Lattices with at least 16 streams per SM (2456 and 4096 streams here) run

@@ -477,3 +477,50 @@ def test_invalid_arguments_rejected(args):
     L, beta, kind = args
     with pytest.raises(ValueError):
         OracleSim(L, 1, 2, beta, kind)
+
+
+# ------------------------------------------------- one site at a time ---
+
+@pytest.mark.parametrize("kind", [RNG_MINSTD, RNG_MT19937, RNG_PR])
+def test_per_site_initial_state_and_stream_words(kind):
+    """The per-site helpers draw the same initial state and stream seeds as the
+    simulator (Eq. (2)): every spin and coupling of an L = 10 lattice, and the
+    first draws of every stream of an L = 66 lattice (8 streams)."""
+    L = 10
+    o = OracleSim(L, 7, 8, 1.0, kind)
+    s, J = o.spins(), o.couplings().reshape(3, -1)
+    for i in range(L ** 3):
+        assert s[i] == oracle.initial_spin(8, i)
+        for d in range(3):
+            assert J[d, i] == oracle.initial_coupling(7, i, d)
+    o = OracleSim(66, 7, 8, 1.0, kind)
+    for t in range(oracle.num_streams(66)):
+        assert np.array_equal(o.peek_draws(t, 300), oracle.stream_draws(kind, oracle.stream_word(8, t), 300))
+
+
+@pytest.mark.parametrize("kind", [RNG_MINSTD, RNG_MT19937, RNG_PR])
+@pytest.mark.parametrize("L", [8, 66])
+def test_sampled_first_sweep_matches_simulator(L, kind):
+    """SampledFirstSweep (the check used at L = 2048, where OracleSim does not
+    fit in memory) against OracleSim after one sweep: every site at L = 8 (one
+    stream), and at L = 66 (8 streams of 545 rows, the last one 541) the sites
+    of the rows at every stream boundary plus 2000 random sites."""
+    beta = 1 / 0.8
+    o = OracleSim(L, 3, 4, beta, kind)
+    o.sweep(1)
+    sp = o.spins()
+    smp = oracle.SampledFirstSweep(L, 3, 4, beta, kind)
+    if L <= 8:
+        sites = [(x, y, z) for z in range(L) for y in range(L) for x in range(L)]
+    else:
+        R = oracle.rows_per_stream(L)
+        rows = sorted({r for t in range(oracle.num_streams(L)) for r in (t * R - 1, t * R) if 0 <= r < L * L})
+        sites = [(x, r % L, r // L) for r in rows for x in range(L)]
+        rng = np.random.default_rng(5)
+        sites += [tuple(int(v) for v in rng.integers(0, L, 3)) for _ in range(2000)]
+    flips = 0
+    for x, y, z in sites:
+        got = smp.after(x, y, z)
+        assert got == sp[x + L * y + L * L * z], (x, y, z)
+        flips += got != smp.initial(x, y, z)
+    assert flips > len(sites) // 10          # the sweep did change many of them
