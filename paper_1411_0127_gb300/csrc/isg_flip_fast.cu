@@ -15,6 +15,13 @@
 // end state x 16807^D is written by its last segment into the handle's other
 // state buffer (rng_alt), so no item can overwrite a state another item has
 // still to read; the host swaps the two buffers after the launch.
+//
+// Consecutive passes are launched with programmatic dependent launch: a warp
+// with no items left signals griddepcontrol.launch_dependents, so the next
+// pass's CTAs can be placed on the SM slots this grid frees, and every CTA
+// starts with griddepcontrol.wait, which returns once the previous grid has
+// completed and its writes are visible.  Small lattices, whose passes last a
+// few microseconds, spend much less of each sweep between launches.
 #include <cstring>
 #include <utility>
 
@@ -46,6 +53,9 @@ struct Segments {
 template <typename Word, int KIND, bool TRIM>
 __global__ void __launch_bounds__(kFastWarps * 32, TRIM ? (KIND == ISG_RNG_MT19937 ? 7 : 8) : 2)
     flip_fast_kernel(FlipArgs a, StreamConst k, Tickets tk, Segments sg) {
+    // Programmatic dependent launch: wait for the previous pass (its spins,
+    // generator states and ticket count) before touching any of them.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     extern __shared__ uint32_t smem[];
     constexpr int kRing = KIND == ISG_RNG_MT19937 ? mt_window(kFastSlack) : 0;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -82,6 +92,9 @@ __global__ void __launch_bounds__(kFastWarps * 32, TRIM ? (KIND == ISG_RNG_MT199
             store_stream<KIND>(a, t, ring, st, lane);
         }
     }
+    // this warp has no more items: the next pass's CTAs may take the SM slots
+    // that this grid's CTAs free (they wait above until this grid completes)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     for (int sh = 16; sh; sh >>= 1) dEsum += __shfl_xor_sync(kFull, dEsum, sh);
     if (lane == 0 && dEsum != 0) atomicAdd((unsigned long long*)a.dE, (unsigned long long)(long long)dEsum);
 }
@@ -148,8 +161,23 @@ static cudaError_t launch_fast_t(isg_sim* h, int colour, cudaStream_t s, int sms
     int64_t blocks = (int64_t)sms * occ;
     const int64_t need = (items + kFastWarps - 1) / kFastWarps;
     if (blocks > need) blocks = need > sms ? need : (sms < blocks ? sms : blocks);  // at least one block per SM
-    flip_fast_kernel<Word, KIND, TRIM><<<(unsigned)blocks, kFastWarps * 32, smem, s>>>(a, k, tk, sg);
-    const cudaError_t e = cudaGetLastError();
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)blocks);
+    lc.blockDim = dim3(kFastWarps * 32);
+    lc.dynamicSmemBytes = smem;
+    lc.stream = s;
+    // Programmatic dependent launch, except for the unsegmented latency form
+    // (MT19937 and Parisi-Rapuano below 16 streams per SM), where the next
+    // pass's CTAs, placed while this grid still runs, made L = 256 MT19937 14 %
+    // slower; it takes L = 32 / 48 / 256 MINSTD from 250 / 104 / 1.62 to
+    // 168 / 54 / 1.34 ps.
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = at;
+    lc.numAttrs = (TRIM || sg.nseg > 1) ? 1 : 0;
+    cudaError_t e = cudaLaunchKernelEx(&lc, flip_fast_kernel<Word, KIND, TRIM>, a, k, tk, sg);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // every warp takes one ticket past the last item before it stops
     h->tickets += (unsigned long long)items + (unsigned long long)blocks * kFastWarps;
