@@ -8,17 +8,19 @@
 //   * on the host their RNG streams are packed into bundles: a lattice with more
 //     than `capacity` streams is one bundle; smaller lattices are packed
 //     together, at most `capacity` streams per bundle;
-//   * CTAs of WARPS warps (one or two per SM) take bundle after bundle (largest
-//     first) from a counter and run all sweeps of the launch on it: warp w
-//     sweeps entries w, w + WARPS, ... of the bundle, and a block barrier
-//     separates the colour passes; no lattice spans two CTAs, so no grid-wide
-//     barrier is needed;
+//   * CTAs of WARPS warps (one or two per SM) take task after task from a
+//     counter: a task is a bundle for all sweeps of the launch or, for a bundle
+//     much longer than the average work per CTA, one of up to 8 consecutive
+//     parts of its sweeps (split_tasks), which waits, bounded, for the previous
+//     part; warp w sweeps entries w, w + WARPS, ... of the bundle, and a block
+//     barrier separates the colour passes; no lattice spans two CTAs at once,
+//     so no grid-wide barrier is needed;
 //   * when a bundle has at most WARPS streams each warp can keep its stream's
-//     generator state (MT19937 words in shared memory) for the whole launch;
-//   * the shape, the capacity and that residency form the execution
-//     configuration (isg_batch_set_config), chosen by the autotuner;
-//   * the bundle counter returns to zero when the last CTA leaves, so the
-//     launch is captured once into a CUDA graph and replayed.
+//     generator state (MT19937 words in shared memory) for the whole task;
+//   * the shape, the capacity, that residency and the words per lane form the
+//     execution configuration (isg_batch_set_config), chosen by the autotuner;
+//   * the task counter and flags return to zero when the last CTA leaves, so
+//     the launch is captured once into a CUDA graph and replayed.
 // Every lattice follows exactly the trajectory it has alone (same map from
 // site to stream and draw), which the tests check against isg_sweep and the
 // CPU oracle.
