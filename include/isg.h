@@ -140,6 +140,26 @@ int isg_write_spins(isg_sim *h, const int8_t *host_in, size_t n, void *cuda_stre
  * one eighth of the bytes to move. */
 int isg_read_spins_packed(const isg_sim *h, uint8_t *host_out, size_t nbytes, void *cuda_stream);
 
+/* Streaming exchange, asynchronous: enqueue on cuda_stream, in this order,
+ *   1. if in != NULL: overwrite the spins from packed bits (the format of
+ *      isg_read_spins_packed; every bit pattern is a valid configuration) and
+ *      restart the energy bookkeeping from the new configuration, on the device;
+ *   2. `sweeps` sweeps (as isg_sweep);
+ *   3. if out != NULL: the packed spins into out;
+ *   4. if E_out != NULL: the tracked energy (int64, as isg_tracked_energy) into
+ *      the host word *E_out.
+ * Nothing is synchronised.  in must stay valid and unchanged, and out / E_out
+ * must not be read, until the stream has passed this call (an event or
+ * cudaStreamSynchronize).  With pinned host memory the copies run on the copy
+ * engines and overlap work on other streams: a loop over a few handles on a few
+ * streams keeps the SMs sweeping while configurations move in and out (the
+ * end-to-end benchmark does this).  nbytes is the size of in and of out (at
+ * least ceil(L^3 / 8) when either is given).  The first call with in or out
+ * allocates a staging buffer of ceil(L^3 / 32) words that the handle keeps.
+ * ISG_ERR_ARG for a NULL handle, sweeps < 0 or short buffers. */
+int isg_exchange_async(isg_sim *h, const uint8_t *in, uint8_t *out, size_t nbytes, int64_t sweeps,
+                       long long *E_out, void *cuda_stream);
+
 /* Overwrite the spins from packed bits in the format of isg_read_spins_packed
  * (sync; every bit pattern is a valid configuration); the tracked energy
  * restarts.  nbytes >= ceil(L^3 / 8) (else ISG_ERR_ARG and nothing changes). */

@@ -46,6 +46,7 @@ SIGNATURES = {
     "isg_write_spins": (_i32, [_vp, _vp, _sz, _vp]),
     "isg_read_spins_packed": (_i32, [_vp, _vp, _sz, _vp]),
     "isg_write_spins_packed": (_i32, [_vp, _vp, _sz, _vp]),
+    "isg_exchange_async": (_i32, [_vp, _vp, _vp, _sz, _i64, _vp, _vp]),
     "isg_read_couplings": (_i32, [_vp, _vp, _sz, _vp]),
     "isg_write_couplings": (_i32, [_vp, _vp, _sz, _vp]),
     "isg_save": (_i32, [_vp, _vp, _vp, _vp]),
@@ -272,6 +273,23 @@ class Sim:
     def write_spins_packed(self, bits: np.ndarray, stream=None):
         bits = np.ascontiguousarray(bits, dtype=np.uint8).reshape(-1)
         _check(lib().isg_write_spins_packed(self._h, _ptr(bits), bits.size, _stream(stream)))
+
+    def exchange_async(self, bits_in: np.ndarray = None, bits_out: np.ndarray = None, sweeps: int = 1,
+                       E_out: np.ndarray = None, stream=None):
+        """Enqueue, without synchronising: packed spins in (optional), `sweeps`
+        sweeps, packed spins out and the tracked energy into E_out[0] (optional;
+        int64).  The arrays must be C-contiguous, should be pinned (torch's
+        pin_memory) for the copies to overlap other work, and must be kept (and
+        bits_in left unchanged) until the stream has passed this call."""
+        nb = (self.N + 7) // 8
+        for a in (bits_in, bits_out):
+            if a is not None and (a.dtype != np.uint8 or not a.flags["C_CONTIGUOUS"] or a.size < nb):
+                raise ValueError("bit buffers must be C-contiguous uint8 arrays of at least ceil(L^3/8) bytes")
+        if E_out is not None and (E_out.dtype != np.int64 or not E_out.flags["C_CONTIGUOUS"] or E_out.size < 1):
+            raise ValueError("E_out must be a C-contiguous int64 array")
+        _check(lib().isg_exchange_async(self._h, None if bits_in is None else _ptr(bits_in),
+                                        None if bits_out is None else _ptr(bits_out), nb, int(sweeps),
+                                        None if E_out is None else _ptr(E_out), _stream(stream)))
 
     def write_spins(self, s: np.ndarray, stream=None):
         s = np.ascontiguousarray(s, dtype=np.int8).reshape(-1)

@@ -97,6 +97,7 @@ static void free_sim(isg_sim* h) {
     dev_free(h, h->rng_pos);
     dev_free(h, h->rng_alt);
     dev_free(h, h->scal);
+    dev_free(h, h->stage);
     delete h;
 }
 
@@ -402,6 +403,60 @@ int isg_read_spins_packed(const isg_sim* hc, uint8_t* out, size_t nbytes, void* 
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     dev_free(h, d);
     return e == cudaSuccess ? ISG_OK : cuda_fail(e, "isg_read_spins_packed");
+}
+
+// Tracking restart on the device (isg_exchange_async): dE := E(now) - E0, so
+// that E0 + dE stays the tracked energy with the host's E0 untouched.
+__global__ void restart_on_device_kernel(long long* scal, long long threeN, long long E0) {
+    scal[0] = 2 * scal[1] - threeN - E0;
+}
+
+// scal[4] = E0 + dE, the tracked energy, for an asynchronous read.
+__global__ void tracked_word_kernel(long long* scal, long long E0) { scal[4] = E0 + scal[0]; }
+
+int isg_exchange_async(isg_sim* h, const uint8_t* in, uint8_t* out, size_t nbytes, int64_t sweeps, long long* E_out,
+                       void* stream) {
+    if (!h || sweeps < 0) { set_error("isg_exchange_async: bad handle or sweeps"); return ISG_ERR_ARG; }
+    const int64_t N = (int64_t)h->L * h->L * h->L;
+    const size_t need = (size_t)((N + 7) / 8);
+    if ((in || out) && nbytes < need) {
+        set_error("isg_exchange_async: buffers hold %zu bytes, %zu needed", nbytes, need);
+        return ISG_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((in || out) && !h->stage) {
+        h->stage = (uint32_t*)dev_alloc(h, (size_t)((N + 31) / 32) * 4);
+        if (!h->stage) { set_error("isg_exchange_async: device allocation failed"); return ISG_ERR_NOMEM; }
+    }
+    cudaError_t e = cudaSuccess;
+    if (in) {
+        e = cudaMemcpyAsync(h->stage, in, need, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = launch_pack_spins_bits(h, h->stage, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->scal + 1, 0, sizeof(long long), s);
+        if (e == cudaSuccess) e = launch_energy(h, h->scal + 1, s);
+        if (e == cudaSuccess) {
+            restart_on_device_kernel<<<1, 1, 0, s>>>(h->scal, 3 * (long long)N, (long long)h->E0);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "isg_exchange_async: spins in");
+    }
+    h->last_stream = s;
+    if (sweeps > 0) {
+        const int rc = isg_sweep(h, sweeps, stream);
+        if (rc) return rc;
+    }
+    if (out) {
+        e = launch_unpack_spins_bits(h, h->stage, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out, h->stage, need, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(e, "isg_exchange_async: spins out");
+    }
+    if (E_out) {
+        tracked_word_kernel<<<1, 1, 0, s>>>(h->scal, (long long)h->E0);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(E_out, h->scal + 4, sizeof(long long), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(e, "isg_exchange_async: energy out");
+    }
+    return ISG_OK;
 }
 
 int isg_write_spins_packed(isg_sim* h, const uint8_t* in, size_t nbytes, void* stream) {

@@ -260,7 +260,9 @@ struct isg_sim {
     uint32_t* rng = nullptr;            // MT: S * 624 ring words; MINSTD: S states
     uint32_t* rng_pos = nullptr;        // MT: S ring positions
     uint32_t* rng_alt = nullptr;        // MINSTD: the other state buffer of segmented passes (see isg_flip_fast.cu)
-    long long* scal = nullptr;          // [0] tracked dE, [1] scratch sum, [2] hash, [3] stream tickets
+    long long* scal = nullptr;          // [0] tracked dE, [1] scratch sum, [2] hash, [3] stream tickets,
+                                        // [4] energy word of isg_exchange_async
+    uint32_t* stage = nullptr;          // packed-spin staging buffer of isg_exchange_async (made on first use)
     unsigned long long tickets = 0;     // value of the stream-ticket counter before the next launch
     int64_t E0 = 0;                     // energy when tracking (re)started
     int64_t sweeps = 0;

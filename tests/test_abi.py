@@ -68,6 +68,7 @@ def test_amsc_create_rejects_bad_arguments_without_touching_the_device(isg):
 def test_other_host_side_checks(isg):
     lib = isg.lib()
     assert lib.isg_read_spins_packed(None, None, 0, None) == isg.ISG_ERR_ARG
+    assert lib.isg_exchange_async(None, None, None, 0, 1, None, None) == isg.ISG_ERR_ARG
     assert lib.isg_batch_set_config(None, 0, 0, 1, 1) == isg.ISG_ERR_ARG
     assert lib.isg_int_rate(3, None) == isg.ISG_ERR_ARG
     assert lib.isg_batch_get_config(None, None, None, None, None) == isg.ISG_ERR_ARG

@@ -315,6 +315,65 @@ def test_spin_io_formats(isg, L):
     np.testing.assert_array_equal(buf[:L**3], s2)
 
 
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("L", [10, 64])
+def test_exchange_async(isg, L, kind):
+    """isg_exchange_async against the oracle: a configuration in, sweeps, the
+    configuration and the tracked energy out, enqueued with no synchronisation;
+    then without an input; then a pipeline of nine exchanges over three handles
+    on three streams equals the same exchanges made one after another."""
+    torch = pytest.importorskip("torch")
+    N, nb = L ** 3, (L ** 3 + 7) // 8
+
+    def pinned(n, dtype):
+        return torch.zeros(n, dtype=dtype).pin_memory().numpy()
+
+    def unpack(bits):
+        return (np.unpackbits(bits, bitorder="little")[:N].astype(np.int8) * 2 - 1).astype(np.int8)
+
+    g, o = pair(isg, L, kind, 1 / 0.9, seed_J=3, seed_spin=4)
+    rng = np.random.default_rng(L)
+    s = np.where(rng.random(N) < 0.5, 1, -1).astype(np.int8)
+    b_in, b_out, E = pinned(nb, torch.uint8), pinned(nb, torch.uint8), pinned(1, torch.int64)
+    b_in[:] = np.packbits(s == 1, bitorder="little")
+    st = torch.cuda.Stream()
+    g.exchange_async(b_in, b_out, 3, E, st)
+    st.synchronize()
+    o.set_spins(s)
+    o.sweep(3)
+    assert np.array_equal(unpack(b_out), o.spins())
+    assert int(E[0]) == o.energy() == g.energy() == g.tracked_energy()
+    g.exchange_async(None, b_out, 2, E, st)
+    st.synchronize()
+    o.sweep(2)
+    assert np.array_equal(unpack(b_out), o.spins())
+    assert int(E[0]) == o.energy()
+
+    def run(pipelined):
+        hs = [isg.Sim(L, 5 + j, 6 + j, 1 / 0.8, kind) for j in range(3)]
+        streams = [torch.cuda.Stream() for _ in range(3)] if pipelined else [torch.cuda.current_stream()] * 3
+        ins = [pinned(nb, torch.uint8) for _ in range(9)]
+        outs = [pinned(nb, torch.uint8) for _ in range(9)]
+        Es = [pinned(1, torch.int64) for _ in range(9)]
+        r = np.random.default_rng(99)
+        for k in range(9):
+            ins[k][:] = r.integers(0, 256, nb, dtype=np.uint8)
+        for k in range(9):
+            hs[k % 3].exchange_async(ins[k] if k % 2 == 0 else None, outs[k], 1 + k % 2, Es[k], streams[k % 3])
+            if not pipelined:
+                torch.cuda.synchronize()
+        torch.cuda.synchronize()
+        res = [(o_.copy(), int(e_[0])) for o_, e_ in zip(outs, Es)]
+        for h in hs:
+            assert h.tracked_energy() == h.energy()
+            h.close()
+        return res
+
+    a, b = run(True), run(False)
+    for (oa, ea), (ob, eb) in zip(a, b):
+        assert np.array_equal(oa, ob) and ea == eb
+
+
 # ------------------------------------------------------------- invariants ---
 
 @pytest.mark.parametrize("kind", KINDS)
