@@ -67,10 +67,10 @@ struct BatchArgs {
     unsigned* ctr;        // [0] next task, [1] CTAs done, [2] sticky error: a dependency wait gave up
     const int4* tasks;    // NULL: task i is bundle i, all its sweeps; else see BundleTasks
     int ntasks;
-    unsigned* done;       // per task: its sweeps are done (first halves only); zeroed at the end of a launch
+    unsigned* done;       // per task: its sweeps are done (set by parts that have a next part); zeroed at launch end
 };
 
-// Iterations of the wait for a first half (each about 0.25 us of sleep): seconds
+// Iterations of the wait for a previous part (each about 0.25 us of sleep): seconds
 // beyond any real wait, after which the kernel sets ctr[2] and skips the task.
 constexpr int kDepWaitLimit = 1 << 24;
 
@@ -570,7 +570,7 @@ int isg_batch_run(isg_batch* b, int64_t sweeps, int group_sweeps, void* cuda_str
     return ISG_OK;
 }
 
-// ISG_ERR_TIMEOUT (once) if a launch gave up waiting for the first half of a
+// ISG_ERR_TIMEOUT (once) if a launch gave up waiting for the previous part of a
 // split bundle: that bundle's lattices then missed sweeps.
 static int batch_check(isg_batch* b, cudaStream_t s) {
     unsigned err = 0;
@@ -579,7 +579,7 @@ static int batch_check(isg_batch* b, cudaStream_t s) {
     if (e != cudaSuccess) return cuda_fail(e, "isg_batch: error check");
     if (err) {
         cudaMemsetAsync(b->d_ctr + 2, 0, sizeof(unsigned), s);
-        set_error("isg_batch: a split bundle's second half gave up waiting for its first half");
+        set_error("isg_batch: a part of a split bundle gave up waiting for the previous part");
         return ISG_ERR_TIMEOUT;
     }
     return ISG_OK;

@@ -56,7 +56,7 @@ cudaError_t prepare_bundle_kernel(int kind, const BundleConfig& cfg);
 // all when bsweeps is NULL), split as `tasks` says (NULL: one task per bundle,
 // in bundle order).  ctr must hold three zeroed words; the kernel returns the
 // first two, and the task flags, to zero when it ends; ctr[2] becomes 1 if a
-// wait for a first half gave up (that second half is then skipped).
+// wait for a previous part gave up (the waiting part is then skipped).
 cudaError_t launch_bundle_kernel(int kind, const BundleConfig& cfg, const FlipArgs* reps, const int2* entries,
                                  const int* boff, const int* bsweeps, int nbundles, int sweeps, unsigned* ctr,
                                  cudaStream_t s, const BundleTasks* tasks = nullptr);
