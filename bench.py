@@ -320,8 +320,8 @@ def rng_section() -> dict:
 
 
 def hbm_peak() -> tuple:
-    """The measured HBM copy rate in GB/s from MEASURED_PEAKS.json, else the
-    profiling recipe's fallback of 6800 GB/s."""
+    """The measured HBM copy rate in GB/s from MEASURED_PEAKS.json, else a
+    fallback of 6800 GB/s (an earlier copy measurement on a GB300)."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         try:
@@ -436,6 +436,21 @@ def run_ours(a, dist: Dist):
         torch.cuda.synchronize()
         plain = p0.elapsed_time(p1) * 1e9 / (a.plain_steps * N)
 
+    # the energy popcount kernel (isg_energy) against HBM: its algorithmic
+    # traffic is every bit plane read once, 4 bits per site (the spins of both
+    # colours and the three forward couplings); the memset and the 8-byte read
+    # of the result ride along inside the events
+    en0, en1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sim.energy(stream)
+    n_en = 20
+    en0.record(stream)
+    for _ in range(n_en):
+        sim.energy(stream)
+    en1.record(stream)
+    torch.cuda.synchronize()
+    en_ms = en0.elapsed_time(en1) / n_en
+    en_gbs = N * 0.5 / (en_ms / 1e3) / 1e9
+
     # end to end through the C-ABI with host buffers, every step: the spin
     # configuration in from pinned host memory, one sweep, the configuration and
     # the tracked energy out.  Main form: packed bits (1 bit per spin, the
@@ -525,6 +540,9 @@ def run_ours(a, dist: Dist):
                      "frac_of_measured_lop3_imad": achieved_tops / int_rates["lop3_imad"],
                      "hbm": {"achieved": hbm_gbs, "peak": hbm_pk, "unit": "GB/s", "frac": hbm_gbs / hbm_pk,
                              "peak_source": hbm_src, "bytes_per_attempt": BYTES_PER_ATTEMPT}},
+        "energy_kernel": {"ms": en_ms, "achieved_gbs": en_gbs, "bytes_per_site": 0.5,
+                          "frac_of_hbm": en_gbs / hbm_peak()[0],
+                          "note": "isg_energy at the same lattice: unsatisfied-bond popcount over all planes"},
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb + 8,
                 "steps": n_pipe,

@@ -52,16 +52,20 @@ static unsigned grid_for(int64_t n, int threads) {
 }
 
 // ---------------------------------------------------------------- energy ---
+// One thread per word of the two colours' planes.  The word count is below 2^31
+// for every L <= 2048 (at most 2 * 2048^2 * 16), so the index arithmetic is
+// 32-bit: three 32-bit divisions per word instead of 64-bit ones.
 template <typename Word>
 __global__ void unsat_kernel(MeasGeom g, long long* out) {
-    const int64_t nw = 2 * g.rows * g.W;
+    const unsigned rows = (unsigned)g.rows, W = (unsigned)g.W;
+    const unsigned nw = 2u * rows * W;
     long long acc = 0;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nw; q += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(q / (g.rows * g.W));
-        const int64_t rem = q - (int64_t)c * g.rows * g.W;
-        const int r = (int)(rem / g.W);
-        const int k = (int)(rem - (int64_t)r * g.W);
-        const int L = g.L, W = g.W;
+    for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < nw; q += gridDim.x * blockDim.x) {
+        const unsigned row = q / W;
+        const int k = (int)(q - row * W);
+        const int c = row >= rows ? 1 : 0;
+        const int r = (int)(row - (unsigned)c * rows);
+        const int L = g.L;
         const int y = r % L, z = r / L;
         const int p = (c + y + z) & 1;
         const int yp = y == L - 1 ? 0 : y + 1, zp = z == L - 1 ? 0 : z + 1;

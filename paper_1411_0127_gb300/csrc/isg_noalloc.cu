@@ -52,11 +52,12 @@ __global__ void static_unsat_kernel(StaticGeom g, unsigned long long* partials) 
     __shared__ unsigned long long warp_sum[8];
     const int64_t q0 = (int64_t)blockIdx.x * kRowsPerPartial;
     const int64_t q1 = q0 + kRowsPerPartial < 2 * g.rows ? q0 + kRowsPerPartial : 2 * g.rows;
-    const int64_t nwords = (q1 - q0) * g.W;
+    const int nwords = (int)((q1 - q0) * g.W);  // a few rows' words: 32-bit index arithmetic
     unsigned long long acc = 0;
-    for (int64_t e = threadIdx.x; e < nwords; e += blockDim.x) {
-        const int64_t q = q0 + e / g.W;
-        const int k = (int)(e % g.W);
+    for (int e = threadIdx.x; e < nwords; e += blockDim.x) {
+        const int eq = e / g.W;
+        const int64_t q = q0 + eq;
+        const int k = e - eq * g.W;
         const int c = q >= g.rows ? 1 : 0;
         const int r = (int)(q - (int64_t)c * g.rows);
         const int L = g.L, W = g.W;
