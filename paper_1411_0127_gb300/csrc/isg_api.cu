@@ -126,6 +126,15 @@ static int energy_sync(const isg_sim* h, int64_t* E, cudaStream_t s) {
     return ISG_OK;
 }
 
+// Tracking restart on the device (isg_exchange_async): dE := E(now) - E0, so
+// that E0 + dE stays the tracked energy with the host's E0 untouched.
+__global__ void restart_on_device_kernel(long long* scal, long long threeN, long long E0) {
+    scal[0] = 2 * scal[1] - threeN - E0;
+}
+
+// scal[4] = E0 + dE, the tracked energy, for an asynchronous read.
+__global__ void tracked_word_kernel(long long* scal, long long E0) { scal[4] = E0 + scal[0]; }
+
 // Restart the energy bookkeeping from the current configuration.
 static int restart_tracking(isg_sim* h, cudaStream_t s) {
     int rc = energy_sync(h, &h->E0, s);
@@ -404,15 +413,6 @@ int isg_read_spins_packed(const isg_sim* hc, uint8_t* out, size_t nbytes, void* 
     dev_free(h, d);
     return e == cudaSuccess ? ISG_OK : cuda_fail(e, "isg_read_spins_packed");
 }
-
-// Tracking restart on the device (isg_exchange_async): dE := E(now) - E0, so
-// that E0 + dE stays the tracked energy with the host's E0 untouched.
-__global__ void restart_on_device_kernel(long long* scal, long long threeN, long long E0) {
-    scal[0] = 2 * scal[1] - threeN - E0;
-}
-
-// scal[4] = E0 + dE, the tracked energy, for an asynchronous read.
-__global__ void tracked_word_kernel(long long* scal, long long E0) { scal[4] = E0 + scal[0]; }
 
 int isg_exchange_async(isg_sim* h, const uint8_t* in, uint8_t* out, size_t nbytes, int64_t sweeps, long long* E_out,
                        void* stream) {
