@@ -157,9 +157,9 @@ class Dist:
 
 
 # ------------------------------------------------------------ our kernels ---
-def traffic_from_profile(kind: str):
-    """DRAM bytes per flip-kernel launch from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
+def profile_fields(kind: str):
+    """The machine-read lines of the committed ncu summary of the flip kernel,
+    if it was taken on the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "flip_L1024_%s.md" % kind)
     src = os.path.join(ROOT, "paper_1411_0127_gb300", "csrc")
     if not os.path.exists(path):
@@ -176,8 +176,27 @@ def traffic_from_profile(kind: str):
             fields[k.strip()] = v.strip()
     if fields.get("kernel_source_sha256_16") != digest:
         return None
+    return fields
+
+
+def traffic_from_profile(kind: str):
+    """DRAM bytes per flip-kernel launch from the committed ncu summary (None if
+    it was not taken on the current kernel source)."""
+    f = profile_fields(kind)
     try:
-        return float(fields["dram_bytes_per_launch"])
+        return float(f["dram_bytes_per_launch"]) if f else None
+    except (KeyError, ValueError):
+        return None
+
+
+def issue_from_profile(kind: str):
+    """ncu's issue-slot utilisation and warp instructions per 32 attempts of the
+    flip kernel from the committed summary (None if stale)."""
+    f = profile_fields(kind)
+    try:
+        return {"issue_active": float(f["issue_active_pct"]) / 100,
+                "warp_instructions_per_32_attempts": float(f["warp_instructions_per_32_attempts"]),
+                "source": "ncu, profiles/flip_L1024_%s.md" % kind} if f else None
     except (KeyError, ValueError):
         return None
 
@@ -538,6 +557,7 @@ def run_ours(a, dist: Dist):
                      "peak_source": "derived: 152 SMs x 128 lanes x 2070 MHz",
                      "measured_int_peaks_tops": int_rates,
                      "frac_of_measured_lop3_imad": achieved_tops / int_rates["lop3_imad"],
+                     "issue": issue_from_profile(w.kind),
                      "hbm": {"achieved": hbm_gbs, "peak": hbm_pk, "unit": "GB/s", "frac": hbm_gbs / hbm_pk,
                              "peak_source": hbm_src, "bytes_per_attempt": BYTES_PER_ATTEMPT}},
         "energy_kernel": {"ms": en_ms, "achieved_gbs": en_gbs, "bytes_per_site": 0.5,
