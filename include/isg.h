@@ -142,8 +142,9 @@ int isg_read_spins_packed(const isg_sim *h, uint8_t *host_out, size_t nbytes, vo
 
 /* Streaming exchange, asynchronous: enqueue on cuda_stream, in this order,
  *   1. if in != NULL: overwrite the spins from packed bits (the format of
- *      isg_read_spins_packed; every bit pattern is a valid configuration) and
- *      restart the energy bookkeeping from the new configuration, on the device;
+ *      isg_read_spins_packed, Sec. 4 bit map; every bit pattern is a valid
+ *      configuration) and restart the energy bookkeeping (Eq. 1) from the new
+ *      configuration, on the device;
  *   2. `sweeps` sweeps (as isg_sweep);
  *   3. if out != NULL: the packed spins into out;
  *   4. if E_out != NULL: the tracked energy (int64, as isg_tracked_energy) into
