@@ -38,6 +38,7 @@ namespace isg {
 
 constexpr int kAmscWarps = 4;
 constexpr int kAmscSlack = 1024;
+constexpr int64_t kAmscDeepStreamsPerSM = 16;  // below: 8 blocks of sites in flight per warp
 
 struct AmscArgs {
     uint32_t* planes;
@@ -138,10 +139,12 @@ __device__ __forceinline__ void site_flip(uint32_t* Sc, const SiteIn& w, uint32_
 }
 
 // One warp per stream; lane l updates the sites l, l + 32, ... of the stream's
-// sequence with the draws of the same index.  Four blocks of 32 sites at a time:
-// the four sites' loads are issued before the draws are made and the flips
-// applied, so each lane has 52 independent loads in flight.
-template <int KIND>
+// sequence with the draws of the same index.  NB blocks of 32 sites at a time:
+// the NB sites' loads are issued before the draws are made and the flips
+// applied, so each lane has 13 NB independent loads in flight.  NB = 4 where
+// HBM binds (many streams); NB = 8 for ensembles with fewer than 16 streams per
+// SM, where each warp's memory latency binds.
+template <int KIND, int NB>
 __global__ void __launch_bounds__(kAmscWarps * 32) amsc_kernel(AmscArgs a, FlipArgs gen, StreamConst k,
                                                                unsigned long long* tickets,
                                                                unsigned long long base) {
@@ -170,29 +173,31 @@ __global__ void __launch_bounds__(kAmscWarps * 32) amsc_kernel(AmscArgs a, FlipA
             q.z = q.r / L;
         }
         int64_t done = 0;
-        for (; done + 128 <= D; done += 128) {
-            SiteIn w[4];
+        for (; done + 32 * NB <= D; done += 32 * NB) {
+            SiteIn w[NB];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < NB; ++j) {
                 site_load(P, L, half, c, q, w[j]);
                 advance(q, 32, half, L);
             }
-            uint32_t d[4];
+            uint32_t d[NB];
             if (KIND == ISG_RNG_MT19937) {
-                mt_quad<kAmscSlack>(B, st.iA, d, k.mul, lane);
+#pragma unroll
+                for (int j = 0; j < NB; j += 4) mt_quad<kAmscSlack>(B, st.iA, d + j, k.mul, lane);
             } else if (KIND == ISG_RNG_PARISI_RAPUANO) {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) d[j] = pr_warp_step(st.xA, st.xB, lane, 32);
+                for (int j = 0; j < NB; ++j) d[j] = pr_warp_step(st.xA, st.xB, lane, 32);
             } else {
+                // lane l holds draws n+l+1 (xA) and n+l+33 (xB); 16807^64 steps both by 64
                 d[0] = st.xA;
                 d[1] = st.xB;
-                d[2] = minstd_mulmod(st.xA, k.a64);
-                d[3] = minstd_mulmod(st.xB, k.a64);
-                st.xA = minstd_mulmod(d[2], k.a64);
-                st.xB = minstd_mulmod(d[3], k.a64);
+#pragma unroll
+                for (int j = 2; j < NB; ++j) d[j] = minstd_mulmod(d[j - 2], k.a64);
+                st.xA = minstd_mulmod(d[NB - 2], k.a64);
+                st.xB = minstd_mulmod(d[NB - 1], k.a64);
             }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) site_flip(P.Sc, w[j], d[j], a);
+            for (int j = 0; j < NB; ++j) site_flip(P.Sc, w[j], d[j], a);
         }
         for (; done < D; done += 32) {
             const int nvalid = D - done < 32 ? (int)(D - done) : 32;
@@ -424,26 +429,34 @@ int isg_amsc_sweep(isg_amsc* m, int64_t n, void* cuda_stream) {
         a.cmp3 = (uint32_t)(((uint64_t)m->thr[3] + 1) / 2);
     }
     const size_t smem = m->kind == ISG_RNG_MT19937 ? (size_t)kAmscWarps * mt_window(kAmscSlack) * 4 : 0;
-    static int occ[3] = {0, 0, 0};
+    static int occ[3][2] = {{0, 0}, {0, 0}, {0, 0}};
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (!occ[m->kind]) {
+    const int deep = m->S < kAmscDeepStreamsPerSM * (int64_t)sms ? 1 : 0;  // NB = 8: latency binds
+    int& oc = occ[m->kind][deep];
+    if (!oc) {
         with_kind(m->kind, [&](auto kc) {
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[m->kind], amsc_kernel<decltype(kc)::value>,
-                                                                 kAmscWarps * 32, smem);
+            return deep ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oc, amsc_kernel<decltype(kc)::value, 8>,
+                                                                        kAmscWarps * 32, smem)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oc, amsc_kernel<decltype(kc)::value, 4>,
+                                                                        kAmscWarps * 32, smem);
         });
-        if (occ[m->kind] < 1) occ[m->kind] = 1;
+        if (oc < 1) oc = 1;
     }
-    int64_t blocks = (int64_t)sms * occ[m->kind];
+    int64_t blocks = (int64_t)sms * oc;
     const int64_t need = (m->S + kAmscWarps - 1) / kAmscWarps;
     if (blocks > need) blocks = need;
     for (int64_t sw = 0; sw < n; ++sw) {
         for (int c = 0; c < 2; ++c) {
             a.c = c;
             const cudaError_t e = with_kind(m->kind, [&](auto kc) {
-                amsc_kernel<decltype(kc)::value><<<(unsigned)blocks, kAmscWarps * 32, smem, s>>>(a, gen, k, m->ctr,
-                                                                                                  m->tickets);
+                if (deep)
+                    amsc_kernel<decltype(kc)::value, 8>
+                        <<<(unsigned)blocks, kAmscWarps * 32, smem, s>>>(a, gen, k, m->ctr, m->tickets);
+                else
+                    amsc_kernel<decltype(kc)::value, 4>
+                        <<<(unsigned)blocks, kAmscWarps * 32, smem, s>>>(a, gen, k, m->ctr, m->tickets);
                 return cudaGetLastError();
             });
             if (e != cudaSuccess) return cuda_fail(e, "isg_amsc_sweep");
