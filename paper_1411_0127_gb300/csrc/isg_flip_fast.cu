@@ -63,11 +63,25 @@ __global__ void __launch_bounds__(kFastWarps * 32, TRIM ? (KIND == ISG_RNG_MT199
     uint32_t* cond = ring + kRing;
     const int64_t items = a.S * sg.nseg;
     int dEsum = 0;
+    // Items come from the ticket counter, except in the MINSTD latency form
+    // (segmented launches), which takes them statically, item u by CTA u mod
+    // grid, so that every SM gets work (L = 256 MINSTD 1.34 -> 1.25 ps, L = 32
+    // 169 -> 163 ps).  The choice is made at compile time: in the MT19937 and
+    // Parisi-Rapuano latency forms even an unused static branch changed the
+    // code enough to cost 6-40 %.
+    constexpr bool kStatic = KIND == ISG_RNG_MINSTD && !TRIM;
+    int64_t u_next = (int64_t)wid * gridDim.x + blockIdx.x;
     for (;;) {
-        unsigned long long v = 0;
-        if (lane == 0) v = atomicAdd(tk.counter, 1ull);
-        v = __shfl_sync(kFull, v, 0);
-        const int64_t u = (int64_t)(v - tk.base);
+        int64_t u;
+        if constexpr (kStatic) {
+            u = u_next;
+            u_next += (int64_t)gridDim.x * kFastWarps;
+        } else {
+            unsigned long long v = 0;
+            if (lane == 0) v = atomicAdd(tk.counter, 1ull);
+            v = __shfl_sync(kFull, v, 0);
+            u = (int64_t)(v - tk.base);
+        }
         if (u >= items) break;
         StreamRegs st;
         if (KIND == ISG_RNG_MINSTD && !TRIM && sg.nseg > 1) {  // segments: latency form only
@@ -179,8 +193,9 @@ static cudaError_t launch_fast_t(isg_sim* h, int colour, cudaStream_t s, int sms
     cudaError_t e = cudaLaunchKernelEx(&lc, flip_fast_kernel<Word, KIND, TRIM>, a, k, tk, sg);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // every warp takes one ticket past the last item before it stops
-    h->tickets += (unsigned long long)items + (unsigned long long)blocks * kFastWarps;
+    // with tickets, every warp takes one ticket past the last item before it stops
+    if (KIND != ISG_RNG_MINSTD || TRIM)
+        h->tickets += (unsigned long long)items + (unsigned long long)blocks * kFastWarps;
     if (sg.nseg > 1) std::swap(h->rng, h->rng_alt);  // the end states are in the other buffer
     return e;
 }
