@@ -40,7 +40,7 @@ INT_LANES_PER_SM = 128                         # 4 SMSPs x 32 lanes, one 32-bit 
 ALU_PEAK_TOPS = SM_COUNT * INT_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12   # 40.27 Tops/s
 OPS_PER_ATTEMPT = {"mt19937": 17, "minstd": 11}  # algorithmic 32-bit integer ops per attempt
 E2E_HANDLES = 4                                # lattices of the pipelined end-to-end exchange
-E2E_PIPE_STEPS = 48                            # its timed steps (12 per lattice)
+E2E_PIPE_STEPS = 192                           # its timed steps (48 per lattice, about 0.3 s)
 BYTES_PER_ATTEMPT = 9 / 8                      # S_c read+write, S_c' once, 6 coupling bits
 
 
@@ -51,7 +51,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--e2e-steps", type=int, default=5)
+    p.add_argument("--e2e-steps", type=int, default=20)
     p.add_argument("--plain-steps", type=int, default=300)
     p.add_argument("--batch-groups", type=int, default=2, help="timed 64-sweep groups of the batched workload (0: skip)")
     p.add_argument("--serve-jobs", type=int, default=16, help="jobs of the serving trace to serve (0: skip)")
