@@ -33,7 +33,8 @@ sys.path.insert(0, ROOT)
 METRIC = "ps per spin-flip attempt (psFlip) at L=1024; batched vs plain psFlip"
 UNIT = "ps/attempt"
 
-# Roofline definitions (derivations in DESIGN.md, section "Roofline").
+# Roofline definitions: the integer issue rate of the SMs, and the algorithmic
+# operations and DRAM bytes of one spin-flip attempt.
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 INT_LANES_PER_SM = 128                         # 4 SMSPs x 32 lanes, one 32-bit op each per clock

@@ -7,7 +7,7 @@
  * colour only read sites of the other colour (Sec. 1), so the result does not
  * depend on the thread count.
  *
- * Conventions fixed here (the paper leaves them open, Readings):
+ * Conventions fixed here (the paper leaves them open):
  *   site i = x + L*y + L*L*z, periodic in x, y, z; colour c(i) = (x+y+z) & 1;
  *   colour 0 ("red") is updated first in every sweep.
  *   coupling J[d][i] joins site i and its +d neighbour (d = 0,1,2 for x,y,z).

@@ -18,7 +18,13 @@
  *   MINSTD                 Sec. 3, Eq. for R_{n+1}   R <- 16807 R mod (2^31-1)
  *   MT19937                Sec. 3 (by name)          Matsumoto & Nishimura 1998
  *
- * Readings where the paper is silent are listed in DESIGN.md ("Readings").
+ * Where the paper is silent this oracle reads it as follows: red (x+y+z even)
+ * is updated first; every attempt consumes one draw, dE <= 0 included; the
+ * site -> (stream, draw) map is the row partition of or_rows_per_stream with
+ * sites in row order and ascending x; couplings, spins and stream seeds come
+ * from the SplitMix64 counter hash; MINSTD's draw is 2x so that one 32-bit
+ * threshold table serves every generator; Parisi-Rapuano starts from 61 hashed
+ * words with the last one made odd.
  */
 #ifndef ISG_ORACLE_H
 #define ISG_ORACLE_H

@@ -8,9 +8,9 @@
 //   * planes: per colour c, S_c, Jx_c, Jy_c, Jz_c, one 32-bit word per site of
 //     that colour, row r = y + L*z holding the L/2 sites x = 2h + ((c+y+z) & 1)
 //     at words r*(L/2) + h;
-//   * draws: the map of the single-sample engine (Sec. 2 of DESIGN: streams of
-//     R(L) rows, sites visited in row order and ascending x, one draw per site
-//     and colour pass), seeded from seed_rng; so sample b follows exactly the
+//   * draws: the map of the single-sample engine (streams of R(L) rows, sites
+//     visited in row order and ascending x, one draw per site and colour
+//     pass), seeded from seed_rng; so sample b follows exactly the
 //     trajectory of a lone lattice with (seed_J[b], seed_spin[b], seed_rng);
 //   * one lane updates one site: it takes its own draw, loads the site word and
 //     the twelve neighbour and coupling words, counts unsatisfied bonds of the 32
