@@ -101,7 +101,7 @@ def _thr_mp(beta):
 
 
 # Parisi-Rapuano (Sec. 3): ira[i] = ira[i-24] + ira[i-55] mod 2^32, R = ira[i] ^ ira[i-61].
-# The seeding is this build's reading (the paper gives none): ira[j] = upper 32
+# The seeding is a reading of the paper, which gives none: ira[j] = upper 32
 # bits of SplitMix64(v, j), j < 61, ira[60] made odd.
 
 def _pr_initial_words(v):
