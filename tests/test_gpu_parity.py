@@ -374,6 +374,43 @@ def test_exchange_async(isg, L, kind):
         assert np.array_equal(oa, ob) and ea == eb
 
 
+def test_empty_work_and_short_buffers(isg):
+    """Zero sweeps change nothing anywhere (lattice, batch, ensemble, exchange);
+    buffers shorter than the configuration are refused before any device work."""
+    import ctypes
+    torch = pytest.importorskip("torch")
+    g = isg.Sim(34, 1, 2, 1 / 0.9, "mt19937")
+    h0, E0 = g.hash(), g.tracked_energy()
+    g.sweep(0)
+    assert g.hash() == h0 and g.tracked_energy() == E0 and g.sweeps_done() == 0
+    E = torch.zeros(1, dtype=torch.int64).pin_memory().numpy()
+    g.exchange_async(None, None, 0, E)
+    torch.cuda.synchronize()
+    assert int(E[0]) == E0 and g.hash() == h0
+    nb = (34 ** 3 + 7) // 8
+    short = np.zeros(nb - 1, dtype=np.uint8)
+    lib = isg.lib()
+    assert lib.isg_exchange_async(g._h, short.ctypes.data, None, short.size, 1, None, None) == isg.ISG_ERR_ARG
+    assert lib.isg_exchange_async(g._h, None, short.ctypes.data, short.size, 1, None, None) == isg.ISG_ERR_ARG
+    assert lib.isg_read_spins_packed(g._h, short.ctypes.data, short.size, None) == isg.ISG_ERR_ARG
+    assert lib.isg_sweep(g._h, -1, None) == isg.ISG_ERR_ARG
+    assert g.hash() == h0 and g.sweeps_done() == 0
+    g.close()
+    b = isg.Batch([16, 20], [1, 2], [3, 4, 5, 6], [1.0, 1.2], "minstd")
+    Eb, Hb = b.tracked()
+    b.run(0)
+    Eb2, Hb2 = b.tracked()
+    assert np.array_equal(Eb, Eb2) and np.array_equal(Hb, Hb2)
+    b.close()
+    from paper_1411_0127_gb300 import workloads
+    J, S = workloads.amsc_seeds(16)
+    m = isg.Amsc(16, J, S, 7, 1 / 0.9, "minstd")
+    Em = m.energies()
+    m.sweep(0)
+    assert np.array_equal(m.energies(), Em)
+    m.close()
+
+
 # ------------------------------------------------------------- invariants ---
 
 @pytest.mark.parametrize("kind", KINDS)
