@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--plain-steps", type=int, default=300)
     p.add_argument("--batch-groups", type=int, default=2, help="timed 64-sweep groups of the batched workload (0: skip)")
     p.add_argument("--serve-jobs", type=int, default=16, help="jobs of the serving trace to serve (0: skip)")
+    p.add_argument("--serve-sustained-jobs", type=int, default=200,
+                   help="jobs of the sustainable-load serving run (0: skip)")
     p.add_argument("--L", type=int, default=0, help="lattice size instead of 1024 (quick runs and tests only)")
     p.add_argument("--other-configs", type=int, default=1, help="also time the L=32/256 and MINSTD lattices (0: skip)")
     p.add_argument("--amsc", type=int, default=1, help="also time the asynchronous multispin ensembles (0: skip)")
@@ -213,24 +215,23 @@ def _stream_block(S: int, R: int, L: int, t0: int, m: int):
 
 
 def cpu_baseline(w, target_s: float = 12.0) -> dict:
-    """The oracle, as it stands, on this host's cores: colour-pass pairs over a
-    block of streams of the same lattice, repeated for about target_s seconds."""
+    """The oracle, as it stands, on this host's cores: whole sweeps (a red and a
+    blue pass over all streams, the threads sharing out the streams of each
+    pass) of the benchmark lattice, repeated for about target_s seconds; and
+    on one core, passes over one stream at a time for about a quarter of that."""
     import oracle
     threads = os.cpu_count() or 1
-    o = oracle.OracleSim(w.L, w.seed_J, w.seed_spin, w.beta, oracle.RNG_MT19937 if w.kind == "mt19937" else 0)
+    kinds = {"minstd": oracle.RNG_MINSTD, "mt19937": oracle.RNG_MT19937, "parisi_rapuano": oracle.RNG_PR}
+    o = oracle.OracleSim(w.L, w.seed_J, w.seed_spin, w.beta, kinds[w.kind])
     S, R = oracle.num_streams(w.L), oracle.rows_per_stream(w.L)
-    m = min(S, 4 * threads)
     t_start = time.perf_counter()
-    attempts = 0
-    t0 = 0
-    while time.perf_counter() - t_start < target_s:
-        t0, t1, n = _stream_block(S, R, w.L, t0, m)
-        o.pass_range(0, t0, t1, threads)
-        o.pass_range(1, t0, t1, threads)
-        attempts += 2 * n
-        t0 = t1
+    sweeps = 0
+    while sweeps == 0 or time.perf_counter() - t_start < target_s:
+        o.pass_range(0, 0, S, threads)
+        o.pass_range(1, 0, S, threads)
+        sweeps += 1
     dt = time.perf_counter() - t_start
-    # the same on one core, for about a quarter of the time
+    attempts = sweeps * w.L ** 3
     t_single, att1, t1s = time.perf_counter(), 0, 0
     while time.perf_counter() - t_single < target_s / 4:
         t1s, t1e, n = _stream_block(S, R, w.L, t1s, 1)
@@ -240,9 +241,9 @@ def cpu_baseline(w, target_s: float = 12.0) -> dict:
         t1s = t1e
     dt1 = time.perf_counter() - t_single
     o.close()
-    return {"value": dt * 1e12 / attempts, "unit": UNIT, "cores": min(threads, m), "kind": "oracle",
-            "sample": "red+blue passes over blocks of %d of the %d streams of the L=%d lattice (%d attempts, "
-                      "%.1f s wall)" % (m, S, w.L, attempts, dt),
+    return {"value": dt * 1e12 / attempts, "unit": UNIT, "cores": min(threads, S), "kind": "oracle",
+            "sample": "%d whole sweeps (red+blue passes over all %d streams) of the L=%d lattice on %d threads "
+                      "(%d attempts, %.1f s wall)" % (sweeps, S, w.L, min(threads, S), attempts, dt),
             "single_core": {"value": dt1 * 1e12 / att1, "unit": UNIT, "cores": 1,
                             "sample": "red+blue passes over one stream at a time (%d attempts, %.1f s wall)"
                                       % (att1, dt1)}}
@@ -379,31 +380,81 @@ def amsc_section(stream) -> dict:
     return out
 
 
-def serving_section(a) -> dict:
-    """The first `--serve-jobs` jobs of the Poisson quench trace (200 jobs/s,
-    L over even multiples of 16 in [32, 512], sweeps log-uniform in [1e2, 1e5],
-    T uniform in [0.5, 1.5], MINSTD or MT19937) served by continuous batching
-    under a 150 GB budget; latency = completion - arrival, queueing included."""
+def _serve(jobs, budget: int, quantum: int, time_limit_s: float = 600.0) -> dict:
+    """Serve `jobs` (arrival times in seconds from the start of the run) and
+    summarise latency (completion - arrival, queueing included) and throughput."""
     import numpy as np
     import paper_1411_0127_gb300 as isg
-    from paper_1411_0127_gb300 import workloads
-    jobs = workloads.serving_trace(a.serve_jobs)
-    srv = isg.Server(150 * 10**9, 64, 4096)
+    srv = isg.Server(budget, quantum, 4096)
     ids = [srv.submit(j.L, j.seed_J, j.seed_spin, 1.0 / j.T, j.kind, j.sweeps, j.arrival) for j in jobs]
-    srv.run(time_limit_s=600)
+    srv.run(time_limit_s=time_limit_s)
     res = [srv.job(i) for i in ids]
     st = srv.stats()
     srv.close()
     lat = np.array([r["latency"] for r in res])
     queue = np.array([r["admit"] - r["arrival"] for r in res])
-    return {"trace": "first %d jobs of the Poisson trace (200 jobs/s, arrival seed 11), %.3g attempts, "
-                     "arrivals over %.3f s" % (len(jobs), st["attempts"], jobs[-1].arrival),
-            "jobs": len(jobs), "finished": sum(r["status"] == 2 for r in res),
+    return {"jobs": len(jobs), "finished": sum(r["status"] == 2 for r in res), "attempts": st["attempts"],
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-            "mean_admission_wait_s": float(queue.mean()),
+            "mean_latency_s": float(lat.mean()), "mean_admission_wait_s": float(queue.mean()),
+            "queueing_share": float(queue.sum() / max(lat.sum(), 1e-12)),
             "aggregate_psflip": st["busy_s"] * 1e12 / max(1, st["attempts"]),
+            "wall_psflip": st["wall_s"] * 1e12 / max(1, st["attempts"]),
+            "attempts_per_s": st["attempts"] / max(st["wall_s"], 1e-12),
             "wall_s": st["wall_s"], "quanta": st["iterations"], "peak_active": st["peak_active"],
-            "peak_bytes": st["peak_bytes"], "budget_bytes": 150 * 10**9, "quantum_sweeps": 64}
+            "peak_bytes": st["peak_bytes"]}
+
+
+SERVE_SWEEP_SCALE = 16     # sweeps of the sustainable-load trace: the trace's count / 16
+SERVE_LOAD = 0.8           # offered load of the sustainable run, as a fraction of measured capacity
+
+
+def serving_section(a) -> dict:
+    """Continuous batching under a 150 GB budget, in two regimes.
+
+    overload: the first `--serve-jobs` jobs of the Poisson quench trace as
+    specified (200 jobs/s, L over even multiples of 16 in [32, 512], sweeps
+    log-uniform in [1e2, 1e5], T uniform in [0.5, 1.5], MINSTD or MT19937),
+    which offers about 100 times what one GPU can sweep.
+
+    sustainable: `--serve-sustained-jobs` jobs with the same L, T and kinds and
+    sweeps divided by SERVE_SWEEP_SCALE, first all at once (the capacity on
+    this job mix: attempts per second of wall time), then as Poisson arrivals
+    at SERVE_LOAD of that capacity; p50 / p99 latency with queueing included."""
+    import dataclasses as dc
+    from paper_1411_0127_gb300 import workloads
+    budget, quantum = 150 * 10**9, 64
+    out = {"budget_bytes": budget, "quantum_sweeps": quantum}
+    if a.serve_jobs > 0:
+        jobs = workloads.serving_trace(a.serve_jobs)
+        r = _serve(jobs, budget, quantum)
+        r["trace"] = ("first %d jobs of the Poisson trace (200 jobs/s, arrival seed 11), %.3g attempts, arrivals "
+                      "over %.3f s" % (len(jobs), r["attempts"], jobs[-1].arrival))
+        out["overload"] = r
+        # the keys of the overload regime also at the top level
+        out.update({k: r[k] for k in ("trace", "jobs", "finished", "p50_latency_s", "p99_latency_s",
+                                      "mean_admission_wait_s", "aggregate_psflip", "wall_s", "quanta",
+                                      "peak_active", "peak_bytes")})
+    n = a.serve_sustained_jobs
+    if n > 0:
+        def scaled(rate):
+            return [dc.replace(j, sweeps=max(1, j.sweeps // SERVE_SWEEP_SCALE))
+                    for j in workloads.serving_trace(n, rate=rate)]
+        burst = [dc.replace(j, arrival=0.0) for j in scaled(200.0)]
+        cap = _serve(burst, budget, quantum)
+        mean_work = sum(j.L ** 3 * j.sweeps for j in burst) / n
+        rate = SERVE_LOAD * cap["attempts_per_s"] / mean_work
+        jobs = scaled(rate)
+        r = _serve(jobs, budget, quantum)
+        r.update({"offered_load": SERVE_LOAD, "arrival_rate_jobs_per_s": rate,
+                  "offered_attempts_per_s": rate * mean_work, "capacity_attempts_per_s": cap["attempts_per_s"],
+                  "trace": "%d jobs of the trace's L, T and kind draws (arrival seed 11) with sweeps / %d "
+                           "(mean %.3g attempts per job), Poisson arrivals at %.3g jobs/s = %.2f of the capacity "
+                           "measured on the same jobs submitted at once" %
+                           (n, SERVE_SWEEP_SCALE, mean_work, rate, SERVE_LOAD)})
+        out["sustainable"] = r
+        out["capacity_burst"] = {k: cap[k] for k in ("jobs", "finished", "attempts", "wall_s", "attempts_per_s",
+                                                       "aggregate_psflip", "p50_latency_s", "p99_latency_s")}
+    return out
 
 
 def run_ours(a, dist: Dist):
@@ -526,7 +577,8 @@ def run_ours(a, dist: Dist):
         h.close()
 
     batched = batched_section(a, stream) if a.batch_groups > 0 else None
-    serving = serving_section(a) if a.serve_jobs > 0 and dist.rank == 0 else None
+    serving = (serving_section(a) if (a.serve_jobs > 0 or a.serve_sustained_jobs > 0) and dist.rank == 0
+               else None)
     others = other_configs_section(stream) if a.other_configs and dist.rank == 0 else None
     rng = rng_section() if a.other_configs and dist.rank == 0 else None
     amsc = amsc_section(stream) if a.amsc and dist.rank == 0 else None
@@ -542,7 +594,8 @@ def run_ours(a, dist: Dist):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic", "impl": "ours",
-        "config": {**workload_config(w), "parallelism": "replicas only (one lattice per GPU)"},
+        "config": {**workload_config(w), "parallelism": "replicas only"},
+        "parallelism": "one lattice per GPU; under torchrun every rank sweeps its own replica",
         "plain_psflip": plain,
         "batched_psflip": batched["psflip"] if batched else None,
         "batched": batched,
@@ -625,7 +678,8 @@ def run_reference(a, dist: Dist):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": total * 1e3 / a.steps, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "int8", "data": "synthetic", "impl": "reference",
-        "config": {**workload_config(w), "parallelism": "host threads over streams"},
+        "config": {**workload_config(w), "parallelism": "replicas only"},
+        "parallelism": "one lattice on the host cores: threads share out the streams of each colour pass",
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": min(threads, m), "kind": "oracle",
                          "sample": "each step: red+blue passes over %d of the %d streams of the L=%d lattice "
                                    "(%d attempts)" % (m, S, w.L, attempts)},

@@ -318,6 +318,13 @@ void isg_amsc_destroy(isg_amsc *m);
  * updates one site word with its own draw.  ISG_ERR_ARG for n < 0. */
 int isg_amsc_sweep(isg_amsc *m, int64_t n, void *cuda_stream);
 
+/* Facts of an ensemble (any output pointer may be NULL): its size L, its
+ * number of RNG streams and rows per stream (the single-lattice partition),
+ * and how many blocks of 32 sites each lane of the sweep kernel keeps in
+ * flight on the current device: 8 when the ensemble has fewer than 16 streams
+ * per SM (latency bound), else 4 (the bandwidth-bound form).  Host only. */
+int isg_amsc_info(const isg_amsc *m, int *L, int64_t *streams, int64_t *rows_per_stream, int *sites_in_flight);
+
 /* Energies E[b] = -sum J s s' of the 32 systems (Eq. 1), counted bit-parallel
  * on the device (sync on cuda_stream).  E must hold 32 entries. */
 int isg_amsc_energies(isg_amsc *m, int64_t *E, void *cuda_stream);
@@ -347,13 +354,13 @@ int isg_int_rate(int mode, double *ops_per_s);
 
 /* ------------------------------------------------------- no allocation --- */
 
-/* The energy of Eq. 1, like isg_energy, for callers that must not allocate
- * device memory when they ask for it: code that enqueues work while a stream
- * is being captured into a CUDA graph (where cudaMalloc is not allowed),
- * real-time loops that cannot take the device-wide synchronisation an
- * allocation may cause, and processes that work inside a device-memory budget
- * fixed up front.  The paper has no counterpart to this call; it exists only
- * for those callers.
+/* The same energy that isg_energy returns, for callers that must not allocate
+ * device memory when they ask for it: real-time loops that cannot take the
+ * device-wide synchronisation an allocation may cause, and processes (or
+ * embedding runtimes with their own memory pool) that work inside a
+ * device-memory budget fixed up front, where any cudaMalloc outside that
+ * budget is an error.  The paper has no counterpart to this call; it exists
+ * only for those callers.
  *
  * Async: enqueues two kernels on cuda_stream and writes E (int64) to the
  * caller's device pointer dev_E; it calls no cudaMalloc, cudaFree or other
@@ -362,8 +369,11 @@ int isg_int_rate(int mode, double *ops_per_s);
  * the process exits.  Lattices needing more partial sums (L > 1448) give
  * ISG_ERR_ARG.  All calls share that array: calls whose kernels overlap on the
  * GPU (e.g. on two streams) race and give wrong results.  The first call on
- * each device looks up the array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture begins. */
+ * each device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current) and keeps it for the life of the process; make
+ * that first call before any stream capture begins.  The kept address assumes
+ * the device's context lives as long as the process: after cudaDeviceReset
+ * (or a released and re-created primary context) the call must not be used. */
 int isg_energy_static_scratch(const isg_sim *h, long long *dev_E, void *cuda_stream);
 
 /* ------------------------------------------------------------- testing --- */

@@ -76,6 +76,7 @@ SIGNATURES = {
     "isg_amsc_destroy": (None, [_vp]),
     "isg_amsc_sweep": (_i32, [_vp, _i64, _vp]),
     "isg_amsc_energies": (_i32, [_vp, _vp, _vp]),
+    "isg_amsc_info": (_i32, [_vp, _vp, _vp, _vp, _vp]),
     "isg_amsc_read_spins": (_i32, [_vp, _i32, _vp, _sz, _vp]),
 }
 
@@ -467,6 +468,14 @@ class Amsc:
 
     def sweep(self, n: int = 1, stream=None):
         _check(lib().isg_amsc_sweep(self._h, int(n), _stream(stream)))
+
+    def info(self) -> dict:
+        """Size, RNG streams, rows per stream and the blocks of 32 sites each
+        lane of the sweep kernel keeps in flight on the current device."""
+        L, nb = ctypes.c_int(), ctypes.c_int()
+        S, R = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().isg_amsc_info(self._h, ctypes.byref(L), ctypes.byref(S), ctypes.byref(R), ctypes.byref(nb)))
+        return {"L": L.value, "streams": S.value, "rows_per_stream": R.value, "sites_in_flight": nb.value}
 
     def energies(self, stream=None) -> np.ndarray:
         E = np.empty(self.SAMPLES, dtype=np.int64)

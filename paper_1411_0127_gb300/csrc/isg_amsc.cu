@@ -313,6 +313,21 @@ __global__ void amsc_unpack_kernel(const uint32_t* planes, int64_t plane_words, 
     }
 }
 
+// Resident blocks per SM of the AMSC kernel of this kind and depth on the
+// current device (cached per device and instantiation).
+static int amsc_occupancy(int kind, int deep, size_t smem) {
+    return with_kind(kind, [&](auto kc) {
+        constexpr int K = decltype(kc)::value;
+        static std::atomic<int> c8[kDeviceSlots], c4[kDeviceSlots];
+        return deep ? occupancy_cached(c8, amsc_kernel<K, 8>, kAmscWarps * 32, smem)
+                    : occupancy_cached(c4, amsc_kernel<K, 4>, kAmscWarps * 32, smem);
+    });
+}
+
+// Sites in flight per lane that a sweep of this ensemble uses on the current
+// device: 8 with fewer than 16 streams per SM, else 4.
+static int amsc_depth(const isg_amsc* m) { return m->S < kAmscDeepStreamsPerSM * (int64_t)sm_count() ? 8 : 4; }
+
 static unsigned amsc_grid(int64_t n, int threads, int64_t per_thread) {
     int64_t b = (n + threads - 1) / threads;
     const int64_t need = (n + threads * per_thread - 1) / (threads * per_thread);
@@ -429,21 +444,9 @@ int isg_amsc_sweep(isg_amsc* m, int64_t n, void* cuda_stream) {
         a.cmp3 = (uint32_t)(((uint64_t)m->thr[3] + 1) / 2);
     }
     const size_t smem = m->kind == ISG_RNG_MT19937 ? (size_t)kAmscWarps * mt_window(kAmscSlack) * 4 : 0;
-    static int occ[3][2] = {{0, 0}, {0, 0}, {0, 0}};
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int deep = m->S < kAmscDeepStreamsPerSM * (int64_t)sms ? 1 : 0;  // NB = 8: latency binds
-    int& oc = occ[m->kind][deep];
-    if (!oc) {
-        with_kind(m->kind, [&](auto kc) {
-            return deep ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oc, amsc_kernel<decltype(kc)::value, 8>,
-                                                                        kAmscWarps * 32, smem)
-                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oc, amsc_kernel<decltype(kc)::value, 4>,
-                                                                        kAmscWarps * 32, smem);
-        });
-        if (oc < 1) oc = 1;
-    }
+    const int sms = sm_count();
+    const int deep = amsc_depth(m) == 8 ? 1 : 0;  // NB = 8: latency binds
+    const int oc = amsc_occupancy(m->kind, deep, smem);
     int64_t blocks = (int64_t)sms * oc;
     const int64_t need = (m->S + kAmscWarps - 1) / kAmscWarps;
     if (blocks > need) blocks = need;
@@ -464,6 +467,15 @@ int isg_amsc_sweep(isg_amsc* m, int64_t n, void* cuda_stream) {
         }
     }
     m->sweeps += n;
+    return ISG_OK;
+}
+
+int isg_amsc_info(const isg_amsc* m, int* L, int64_t* streams, int64_t* rows_per_stream, int* sites_in_flight) {
+    if (!m) { set_error("isg_amsc_info: NULL handle"); return ISG_ERR_ARG; }
+    if (L) *L = m->L;
+    if (streams) *streams = m->S;
+    if (rows_per_stream) *rows_per_stream = m->R;
+    if (sites_in_flight) *sites_in_flight = amsc_depth(m);
     return ISG_OK;
 }
 

@@ -25,6 +25,31 @@ int cuda_fail(cudaError_t e, const char* what) {
     return ISG_ERR_CUDA;
 }
 
+int current_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        dev = 0;
+    }
+    return dev < 0 ? 0 : dev;
+}
+
+int sm_count() {
+    static std::atomic<int> cache[kDeviceSlots];
+    const int dev = current_device();
+    if (dev < kDeviceSlots) {
+        const int v = cache[dev].load(std::memory_order_relaxed);
+        if (v > 0) return v;
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        sms = 1;
+    }
+    if (dev < kDeviceSlots) cache[dev].store(sms, std::memory_order_relaxed);
+    return sms;
+}
+
 static void* default_alloc(size_t n, void*) {
     void* p = nullptr;
     return cudaMalloc(&p, n) == cudaSuccess ? p : nullptr;

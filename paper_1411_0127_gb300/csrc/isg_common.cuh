@@ -10,6 +10,7 @@
 //   once; a site's -d coupling is the +d coupling of its -d neighbour.
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <type_traits>
 #include <cuda_runtime.h>
@@ -275,6 +276,31 @@ struct isg_sim {
 };
 
 namespace isg {
+// Per-device launch facts.  A process may drive several devices, so SM counts
+// and occupancies are cached per device ordinal (up to kDeviceSlots devices;
+// beyond that they are queried on every call).
+constexpr int kDeviceSlots = 64;
+int current_device();   // cudaGetDevice, 0 if it fails
+int sm_count();         // SMs of the current device
+
+// Resident blocks per SM of `kernel` with the given block shape on the current
+// device, looked up once per device in `cache` (one array per instantiation).
+template <class Kernel>
+int occupancy_cached(std::atomic<int> (&cache)[kDeviceSlots], Kernel kernel, int threads, size_t smem) {
+    const int dev = current_device();
+    if (dev < kDeviceSlots) {
+        const int v = cache[dev].load(std::memory_order_relaxed);
+        if (v > 0) return v;
+    }
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem) != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        occ = 1;
+    }
+    if (dev < kDeviceSlots) cache[dev].store(occ, std::memory_order_relaxed);
+    return occ;
+}
+
 // Host-side helpers shared by the .cu files of the library.
 void set_error(const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);

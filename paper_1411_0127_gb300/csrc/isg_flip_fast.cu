@@ -164,12 +164,8 @@ static cudaError_t launch_fast_t(isg_sim* h, int colour, cudaStream_t s, int sms
     tk.base = h->tickets;
     constexpr int kRing = KIND == ISG_RNG_MT19937 ? mt_window(kFastSlack) : 0;
     const size_t smem = (size_t)kFastWarps * (kRing + 2 * kCondWords) * sizeof(uint32_t);
-    static int occ = 0;  // resident blocks per SM of this instantiation
-    if (occ == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, flip_fast_kernel<Word, KIND, TRIM>,
-                                                                      kFastWarps * 32, smem);
-        if (e != cudaSuccess || occ < 1) occ = 1;
-    }
+    static std::atomic<int> occ_cache[kDeviceSlots];  // resident blocks per SM of this instantiation
+    const int occ = occupancy_cached(occ_cache, flip_fast_kernel<Word, KIND, TRIM>, kFastWarps * 32, smem);
     const Segments sg = plan_segments(h, (int64_t)sms * occ * kFastWarps, !TRIM);
     const int64_t items = h->S * sg.nseg;
     int64_t blocks = (int64_t)sms * occ;
@@ -201,12 +197,7 @@ static cudaError_t launch_fast_t(isg_sim* h, int colour, cudaStream_t s, int sms
 }
 
 cudaError_t launch_flip_fast(isg_sim* h, int colour, cudaStream_t s) {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    }
+    const int sms = sm_count();
     const bool trim = h->S >= kTrimStreamsPerSM * sms;
     return with_kind(h->kind, [&](auto kind) {
         constexpr int K = decltype(kind)::value;

@@ -2,14 +2,13 @@
 // without allocating any memory.
 //
 // Some callers must not allocate device memory at the moment they ask for the
-// energy: code that enqueues work while a stream is being captured into a CUDA
-// graph (cudaMalloc is not allowed there), real-time loops that cannot afford
-// the device-wide synchronisation an allocation may cause, and processes that
-// run under a fixed device-memory budget handed out up front.  isg_energy
-// reduces into a word owned by the handle; this variant keeps its per-block
-// partial sums in a fixed array compiled into the library instead, so the call
-// only launches kernels and never calls cudaMalloc, cudaFree or any allocating
-// routine.
+// energy: real-time loops that cannot afford the device-wide synchronisation
+// an allocation may cause, and processes or embedding runtimes that hand out
+// their device memory from a budget fixed up front, where any allocation
+// outside it is an error.  isg_energy reduces into a word owned by the handle;
+// this variant keeps its per-block partial sums in a fixed array compiled into
+// the library instead, so the call only launches kernels and never calls
+// cudaMalloc, cudaFree or any allocating routine.
 //
 // Limits and sharing rules:
 //   * the array holds kStaticPartials = 8192 partial sums (64 KiB per device);
@@ -22,8 +21,10 @@
 //     kernels overlap on the GPU (for instance on two streams) race and give
 //     wrong results;
 //   * the first call on a device looks up the array's device address with
-//     cudaGetSymbolAddress (once per device, with that device current); make
-//     that first call before any stream capture begins.
+//     cudaGetSymbolAddress (once per device, with that device current) and
+//     keeps it; make that first call before any stream capture begins.  The
+//     kept address assumes that the device's context lives until the process
+//     exits (no cudaDeviceReset in between).
 #include <mutex>
 
 #include "isg_common.cuh"
@@ -44,8 +45,8 @@ struct StaticGeom {
 };
 
 // Block b counts the unsatisfied forward bonds of rows [512 b, 512 b + 512) of
-// the 2 * rows rows of both colours (Eq. 1 with the Sec. 4 bit map) and writes
-// the count to partials[b].
+// the 2 * rows rows of both colours (the count isg_energy makes) and writes the
+// count to partials[b].
 template <typename Word>
 __global__ void static_unsat_kernel(StaticGeom g, unsigned long long* partials) {
     constexpr int w = 8 * sizeof(Word);

@@ -7,8 +7,9 @@ seed_rng.  The oracle runs that lone lattice (OracleSim(..., seed_rng=R)); spins
 and energies must agree bit for bit, every system, after every checked sweep.
 
 Sizes: L = 4 (two sites per row and colour), L = 10 and 50 (ragged tails of the
-32-site blocks), L = 50 and 64 (several streams), L = 256 (64 streams of 1024
-rows); beta = inf (only u >= 3 flips)."""
+32-site blocks), L = 50 and 64 (several streams), L = 256 (512 streams of 128
+rows), L = 432 and 512 (2456 and 4096 streams: the kernel form with four blocks
+of sites in flight per lane); beta = inf (only u >= 3 flips)."""
 import math
 
 import numpy as np
@@ -89,6 +90,40 @@ def test_large_lattice_against_single_lattice_handles(isg):
         if b in (0, 13, 31):
             np.testing.assert_array_equal(m.spins(b), h.read_spins())
         h.close()
+
+
+@pytest.mark.parametrize("L,kind,sweeps", [(432, "mt19937", 3), (512, "minstd", 2), (432, "parisi_rapuano", 2)])
+def test_bandwidth_form_against_lone_lattices_and_oracle(isg, L, kind, sweeps):
+    """The form of the sweep kernel that ensembles with at least 16 streams per
+    SM take (four blocks of 32 sites in flight per lane, the L = 1024
+    benchmark's form): all 32 energies against lone GPU handles seeded the same
+    way, the spins of systems 0, 13 and 31 against those handles, and system 5
+    directly against the oracle.  L = 432 has a 32-site tail block in every
+    stream (76 rows of 216 sites; the last stream 44 rows); L = 512 none."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    beta = 1 / 0.9
+    J, S = seeds(L + 1)
+    R = 0xA5C0 + L
+    m = isg.Amsc(L, J, S, R, beta, kind)
+    info = m.info()
+    assert info["streams"] >= 16 * sms, info
+    assert info["sites_in_flight"] == 4, info
+    m.sweep(sweeps)
+    E = m.energies()
+    for b in range(32):
+        h = isg.Sim(L, J[b], S[b], beta, kind, seed_rng=R)
+        h.sweep(sweeps)
+        assert E[b] == h.energy(), (b, kind)
+        if b in (0, 13, 31):
+            np.testing.assert_array_equal(m.spins(b), h.read_spins(), err_msg="system %d" % b)
+        h.close()
+    o = OracleSim(L, J[5], S[5], beta, isg.RNG_KINDS[kind], seed_rng=R)
+    o.sweep(sweeps, threads=16)
+    np.testing.assert_array_equal(m.spins(5), o.spins())
+    assert E[5] == o.energy() == o.tracked_energy()
+    o.close()
+    m.close()
 
 
 def test_shared_draws_make_identical_systems_move_together(isg):

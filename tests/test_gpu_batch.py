@@ -105,6 +105,45 @@ def test_full_batch_workload_sampled(isg):
                 assert Q[s] == o0.overlap(o), (v, s)
 
 
+@pytest.mark.slow
+def test_full_batch_workload_every_replica(isg):
+    """The 512-sample workload at the benchmark's launch configuration (one
+    graph-replayed persistent launch of 64 sweeps): the tracked energy and the
+    hash of all 1024 replicas and the overlap of all 512 samples against the
+    oracle.  The oracles run 16 at a time on host threads (the ctypes calls
+    release the interpreter lock), one thread each."""
+    import concurrent.futures as cf
+    import os
+    from paper_1411_0127_gb300 import workloads
+    samples = workloads.batch_samples()
+    b = isg.Batch([x.L for x in samples], [x.seed_J for x in samples], [v for x in samples for v in x.seed_spin],
+                  [1.0 / x.T for x in samples], "mt19937")
+    b.run(64, group_sweeps=64)
+    E, Q = b.measure()
+    Et, H = b.tracked()
+    assert np.array_equal(E, Et)
+    b.close()
+
+    def one(s):
+        x = samples[s]
+        o = [OracleSim(x.L, x.seed_J, x.seed_spin[j], 1.0 / x.T, oracle.RNG_MT19937) for j in range(2)]
+        for oj in o:
+            oj.sweep(64, threads=1)
+        r = (o[0].tracked_energy(), o[1].tracked_energy(), o[0].hash(), o[1].hash(), o[0].overlap(o[1]))
+        for oj in o:
+            oj.close()
+        return r
+
+    order = sorted(range(len(samples)), key=lambda s: -samples[s].L)   # largest first
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        res = dict(zip(order, ex.map(one, order)))
+    for s in range(len(samples)):
+        e0, e1, h0, h1, q = res[s]
+        assert E[2 * s] == e0 and E[2 * s + 1] == e1, (s, samples[s].L)
+        assert int(H[2 * s]) == h0 and int(H[2 * s + 1]) == h1, (s, samples[s].L)
+        assert Q[s] == q, (s, samples[s].L)
+
+
 def test_batch_rejects_bad_arguments(isg):
     with pytest.raises(isg.IsgError):
         isg.Batch([16, 15], [1, 2], [1, 2, 3, 4], [1.0, 1.0])

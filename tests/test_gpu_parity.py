@@ -168,12 +168,18 @@ def test_small_workload_every_sweep(isg):
     assert np.array_equal(g.read_spins(), o.spins())
 
 
-@pytest.mark.parametrize("kind", KINDS)
-def test_medium_workload_powers_of_two(isg, kind):
-    """L = 256, T = 0.7: energy and hash at sweeps 2^k, k = 0..10."""
+@pytest.mark.parametrize("kind,kmax", [
+    pytest.param("minstd", 13, marks=pytest.mark.slow),
+    pytest.param("mt19937", 13, marks=pytest.mark.slow),
+    ("parisi_rapuano", 10),
+])
+def test_medium_workload_powers_of_two(isg, kind, kmax):
+    """L = 256, T = 0.7: energy and hash at sweeps 2^k, k = 0..kmax.  MINSTD
+    and MT19937 run the workload's stated length (10^4 sweeps, measured at
+    every 2^k up to 2^13 = 8192); the third generator to 2^10."""
     g, o = pair(isg, 256, kind, 1 / 0.7)
     done = 0
-    for k in range(11):
+    for k in range(kmax + 1):
         n = 2**k - done
         g.sweep(n)
         o.sweep(n, threads=16)
@@ -181,19 +187,28 @@ def test_medium_workload_powers_of_two(isg, kind):
         assert g.tracked_energy() == o.tracked_energy(), k
         assert g.hash() == o.hash(), k
     assert g.energy() == o.energy()
+    assert np.array_equal(g.read_spins(), o.spins())
 
 
-def test_large_workload_two_sweeps(isg):
+@pytest.mark.slow
+def test_large_workload_powers_of_two(isg):
     """L = 1024, MT19937, T = 0.9 -- the benchmarked configuration, launched as
-    the benchmark launches it: two sweeps against the oracle, all spins."""
+    the benchmark launches it: tracked energy and hash against the oracle at
+    sweeps 1, 2, 4, ..., 32, the energy from scratch and all 2^30 spins at the
+    end."""
     from paper_1411_0127_gb300 import workloads
     w = workloads.LARGE
     g, o = pair(isg, w.L, w.kind, w.beta, w.seed_J, w.seed_spin)
     assert g.hash() == o.hash()
-    g.sweep(2)
-    o.sweep(2, threads=16)
-    assert g.tracked_energy() == o.tracked_energy()
-    assert g.hash() == o.hash()
+    done = 0
+    for k in range(6):
+        n = 2**k - done
+        g.sweep(n)
+        o.sweep(n, threads=16)
+        done = 2**k
+        assert g.tracked_energy() == o.tracked_energy(), k
+        assert g.hash() == o.hash(), k
+    assert g.energy() == o.energy()
     assert np.array_equal(g.read_spins(), o.spins())
 
 

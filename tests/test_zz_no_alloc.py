@@ -1,14 +1,18 @@
 """isg_energy_static_scratch: the energy for callers that must not allocate.
 
 Some callers cannot let the library call cudaMalloc when they ask for the
-energy (work enqueued during CUDA-graph capture, real-time loops, fixed device
-memory budgets).  This entry point keeps its scratch in a fixed array compiled
-into the library; here it is called through the C-ABI and must give exactly
-the value isg_energy gives (integer energies: tolerance zero), on two calls in
-a row and again after more sweeps.  The file is named so that pytest collects
-it after every other test file.
+energy: real-time loops that cannot take the device-wide synchronisation an
+allocation may cause, and processes or embedding runtimes that work inside a
+device-memory budget fixed up front.  This entry point keeps its scratch in a
+fixed array compiled into the library; here it is called through the C-ABI and
+must give exactly the value isg_energy gives and the oracle's energy of the
+same trajectory (integer energies: tolerance zero), on two calls in a row and
+again after more sweeps.  The file is named so that pytest collects it after
+every other test file.
 """
 import pytest
+
+from oracle import OracleSim
 
 pytestmark = pytest.mark.gpu
 
@@ -33,23 +37,28 @@ def _static_energy(isg, sim, out, stream):
 def test_static_scratch_energy_equals_isg_energy(isg, L, kind):
     import torch
     stream = torch.cuda.current_stream()
-    sim = isg.Sim(L, 3, 4, 1 / 0.9, kind)
+    beta = 1 / 0.9
+    sim = isg.Sim(L, 3, 4, beta, kind)
+    orc = OracleSim(L, 3, 4, beta, isg.RNG_KINDS[kind])
     out = torch.full((4,), -1, dtype=torch.int64, device="cuda")
     sim.sweep(3, stream)
+    orc.sweep(3, threads=8)
     _static_energy(isg, sim, out[0], stream)          # two calls in a row
     _static_energy(isg, sim, out[1], stream)
     torch.cuda.synchronize()
     E = sim.energy(stream)
-    assert int(out[0].item()) == E
+    assert int(out[0].item()) == E == orc.energy()
     assert int(out[1].item()) == E
     sim.sweep(5, stream)                               # the shared array is reused
+    orc.sweep(5, threads=8)
     _static_energy(isg, sim, out[2], stream)
     _static_energy(isg, sim, out[3], stream)
     torch.cuda.synchronize()
     E2 = sim.energy(stream)
     assert int(out[2].item()) == E2 == int(out[3].item())
-    assert E2 == sim.tracked_energy()
+    assert E2 == sim.tracked_energy() == orc.energy()
     sim.close()
+    orc.close()
 
 
 def test_static_scratch_rejects_lattices_beyond_its_array(isg):
