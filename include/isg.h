@@ -320,10 +320,14 @@ int isg_amsc_sweep(isg_amsc *m, int64_t n, void *cuda_stream);
 
 /* Facts of an ensemble (any output pointer may be NULL): its size L, its
  * number of RNG streams and rows per stream (the single-lattice partition),
- * and how many blocks of 32 sites each lane of the sweep kernel keeps in
- * flight on the current device: 8 when the ensemble has fewer than 16 streams
- * per SM (latency bound), else 4 (the bandwidth-bound form).  Host only. */
-int isg_amsc_info(const isg_amsc *m, int *L, int64_t *streams, int64_t *rows_per_stream, int *sites_in_flight);
+ * and the form of the sweep kernel on the current device: 0 = the chunked form
+ * (rows of a multiple of 128 sites per colour, i.e. L a multiple of 256: each
+ * lane updates four consecutive sites of a 128-site chunk with 16-byte loads,
+ * the next chunk's words in flight while the current one is computed), else
+ * the site-strided form with `form` blocks of 32 sites in flight per lane: 8
+ * when the ensemble has fewer than 16 streams per SM (latency bound), 4
+ * otherwise.  Host only. */
+int isg_amsc_info(const isg_amsc *m, int *L, int64_t *streams, int64_t *rows_per_stream, int *form);
 
 /* Energies E[b] = -sum J s s' of the 32 systems (Eq. 1), counted bit-parallel
  * on the device (sync on cuda_stream).  E must hold 32 entries. */

@@ -470,12 +470,13 @@ class Amsc:
         _check(lib().isg_amsc_sweep(self._h, int(n), _stream(stream)))
 
     def info(self) -> dict:
-        """Size, RNG streams, rows per stream and the blocks of 32 sites each
-        lane of the sweep kernel keeps in flight on the current device."""
+        """Size, RNG streams, rows per stream and the sweep kernel's form on the
+        current device (0: staged by bulk copies; 4 or 8: register form with
+        that many blocks of 32 sites in flight per lane)."""
         L, nb = ctypes.c_int(), ctypes.c_int()
         S, R = ctypes.c_int64(), ctypes.c_int64()
         _check(lib().isg_amsc_info(self._h, ctypes.byref(L), ctypes.byref(S), ctypes.byref(R), ctypes.byref(nb)))
-        return {"L": L.value, "streams": S.value, "rows_per_stream": R.value, "sites_in_flight": nb.value}
+        return {"L": L.value, "streams": S.value, "rows_per_stream": R.value, "form": nb.value}
 
     def energies(self, stream=None) -> np.ndarray:
         E = np.empty(self.SAMPLES, dtype=np.int64)

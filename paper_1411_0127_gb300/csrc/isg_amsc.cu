@@ -12,9 +12,12 @@
 //     visited in row order and ascending x, one draw per site and colour
 //     pass), seeded from seed_rng; so sample b follows exactly the
 //     trajectory of a lone lattice with (seed_J[b], seed_spin[b], seed_rng);
-//   * one lane updates one site: it takes its own draw, loads the site word and
-//     the twelve neighbour and coupling words, counts unsatisfied bonds of the 32
-//     samples with the bit-sliced adder, and flips with the broadcast masks.
+//   * a lane takes a site's draw, loads the site word and the twelve neighbour
+//     and coupling words, counts unsatisfied bonds of the 32 samples with the
+//     bit-sliced adder, and flips with the broadcast masks; rows of a multiple
+//     of 128 sites take the chunked form (four consecutive sites per lane,
+//     16-byte loads, the next chunk's loads in flight), other sizes the
+//     site-strided form (sites l, l + 32, ... of the stream per lane).
 #include <new>
 
 #include "isg_stream.cuh"
@@ -226,6 +229,241 @@ __global__ void __launch_bounds__(kAmscWarps * 32) amsc_kernel(AmscArgs a, FlipA
     }
 }
 
+// ---------------------------------------------------------------------------
+// Chunked forms for lattices whose rows hold a multiple of 128 sites per
+// colour (L a multiple of 256).  A warp still owns one stream at a time and
+// makes its draws 128 at a time in stream order (block j, lane l: site 32j + l
+// of the chunk), but lane l updates the four consecutive sites h0+4l ..
+// h0+4l+3 of the chunk, so every plane segment the chunk needs is one 16-byte
+// access per lane:
+//   S_c, Jx_c, Jy_c, Jz_c of the chunk's sites (the spins read and written);
+//   S_n and Jx_n of the same row (the x neighbours and the -x coupling at h);
+//   S_n of rows y+1 and y-1, Jy_n of row y-1; S_n of rows z+1 and z-1, Jz_n of
+//   row z-1;
+// and one halo word of S_n (and, for p = 0, of Jx_n) next to the chunk on the
+// side of the row's shifted x neighbour: h0-1 when p = 0, h0+128 when p = 1,
+// wrapping around the row.  Each lane takes its four sites' levels out of the
+// warp-wide ballots of the four blocks of draws.  The next chunk's words are
+// loaded into registers (two buffers) before the current chunk's draws are
+// made, so every lane keeps twelve 16-byte loads in flight while it computes.
+constexpr int kChunk = 128;  // sites per chunk (4 per lane)
+
+// Position of a chunk: row r = y + L z, first site h0.
+struct RowCursor {
+    int r, h0, y, z;
+};
+
+__device__ __forceinline__ RowCursor cursor_at(const AmscArgs& a, int64_t r0) {
+    RowCursor c;
+    c.r = (int)r0;
+    c.h0 = 0;
+    c.y = c.r % a.L;
+    c.z = c.r / a.L;
+    return c;
+}
+
+__device__ __forceinline__ void cursor_next(RowCursor& c, int half, int L) {
+    c.h0 += kChunk;
+    if (c.h0 == half) {
+        c.h0 = 0;
+        ++c.r;
+        if (++c.y == L) {
+            c.y = 0;
+            ++c.z;
+        }
+    }
+}
+
+// Word offsets (within a plane) of a chunk's rows and of its halo word.
+struct ChunkOffs {
+    int o, yp, ym, zp, zm, halo, p;
+};
+
+__device__ __forceinline__ ChunkOffs chunk_offs(const AmscArgs& a, const RowCursor& c) {
+    const int half = a.half, L = a.L;
+    ChunkOffs q;
+    q.o = c.r * half + c.h0;
+    q.yp = q.o + (c.y == L - 1 ? 1 - L : 1) * half;
+    q.ym = q.o + (c.y == 0 ? L - 1 : -1) * half;
+    const int Lh = L * half;
+    q.zp = q.o + (c.z == L - 1 ? -(L - 1) * Lh : Lh);
+    q.zm = q.o + (c.z == 0 ? (L - 1) * Lh : -Lh);
+    q.p = (a.c + c.y + c.z) & 1;
+    q.halo = c.r * half + (q.p == 0 ? (c.h0 == 0 ? half - 1 : c.h0 - 1) : (c.h0 + kChunk == half ? 0 : c.h0 + kChunk));
+    return q;
+}
+
+// A chunk's words as one lane sees them.
+struct ChunkData {
+    uint4 s, jx, jy, jz, na, jxn, syp, sym, jym, szp, szm, jzm;
+    uint32_t hs, hj;  // halo words of S_n and Jx_n (meaningful in the edge lane only)
+    int o, p;
+};
+
+__device__ __forceinline__ uint4 ldg4(const uint32_t* p) { return __ldg((const uint4*)p); }
+
+__device__ __forceinline__ void chunk_load(const AmscPtrs& P, const ChunkOffs& q, int lane, ChunkData& d) {
+    const int l4 = 4 * lane;
+    d.s = *(const uint4*)(P.Sc + q.o + l4);  // read here and written back by this lane only
+    d.jx = ldg4(P.Jxc + q.o + l4);
+    d.jy = ldg4(P.Jyc + q.o + l4);
+    d.jz = ldg4(P.Jzc + q.o + l4);
+    d.na = ldg4(P.Sn + q.o + l4);
+    d.jxn = ldg4(P.Jxn + q.o + l4);
+    d.syp = ldg4(P.Sn + q.yp + l4);
+    d.sym = ldg4(P.Sn + q.ym + l4);
+    d.jym = ldg4(P.Jyn + q.ym + l4);
+    d.szp = ldg4(P.Sn + q.zp + l4);
+    d.szm = ldg4(P.Sn + q.zm + l4);
+    d.jzm = ldg4(P.Jzn + q.zm + l4);
+    const bool edge = lane == (q.p == 0 ? 0 : 31);
+    d.hs = edge ? __ldg(P.Sn + q.halo) : 0u;
+    d.hj = edge && q.p == 0 ? __ldg(P.Jxn + q.halo) : 0u;
+    d.o = q.o;
+    d.p = q.p;
+}
+
+__device__ __forceinline__ uint32_t comp(const uint4& v, int i) { return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w)); }
+
+// all ones if bit i of v is set, else zero
+__device__ __forceinline__ uint32_t bitmask(uint32_t v, int i) { return (uint32_t)((int32_t)(v << (31 - i)) >> 31); }
+
+// Updates the lane's four sites of a chunk (parity P) with the levels of their
+// draws (lo4 / hi4: bits 4l..4l+3 of the chunk's lo / hi ballot streams) and
+// writes them back with one 16-byte store.  A site flips when u + level >= 3
+// (Sec. 4 with dE = 12 - 4u: u >= 3 always, u = 2 when d < thr1, u = 1 when
+// d < thr2, u = 0 when d < thr3).
+template <int P>
+__device__ __forceinline__ void chunk_update(const ChunkData& d, uint32_t* Sc, uint32_t lo4, uint32_t hi4, int lane) {
+    // the shifted x neighbour (and, for p = 0, the -x coupling) of the lane's
+    // edge site comes from the next lane over, or the halo at the chunk's edge
+    uint32_t edge_s, edge_j = 0;
+    if (P == 0) {
+        edge_s = __shfl_up_sync(kFull, d.na.w, 1);
+        edge_j = __shfl_up_sync(kFull, d.jxn.w, 1);
+        if (lane == 0) {
+            edge_s = d.hs;
+            edge_j = d.hj;
+        }
+    } else {
+        edge_s = __shfl_down_sync(kFull, d.na.x, 1);
+        if (lane == 31) edge_s = d.hs;
+    }
+    const uint32_t L4 = lo4 | hi4, L8 = hi4, L12 = lo4 & hi4;
+    uint32_t out[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint32_t sv = comp(d.s, i), nav = comp(d.na, i);
+        uint32_t ns, jxm;
+        if (P == 0) {
+            ns = i == 0 ? edge_s : comp(d.na, i - 1);
+            jxm = i == 0 ? edge_j : comp(d.jxn, i - 1);
+        } else {
+            ns = i == 3 ? edge_s : comp(d.na, i + 1);
+            jxm = comp(d.jxn, i);
+        }
+        const uint32_t sxp = P == 0 ? nav : ns, sxm = P == 0 ? ns : nav;
+        uint32_t u0, u1, u2;
+        Logic<uint32_t>::count6(comp(d.jx, i) ^ sv ^ sxp, jxm ^ sv ^ sxm, comp(d.jy, i) ^ sv ^ comp(d.syp, i),
+                                comp(d.jym, i) ^ sv ^ comp(d.sym, i), comp(d.jz, i) ^ sv ^ comp(d.szp, i),
+                                comp(d.jzm, i) ^ sv ^ comp(d.szm, i), u0, u1, u2);
+        // u + level >= 3, level = c4 + c8 + c12 as all-ones / all-zeros masks
+        const uint32_t c4 = bitmask(L4, i), c8 = bitmask(L8, i), c12 = bitmask(L12, i);
+        out[i] = sv ^ (u2 | (u1 & (u0 | c4)) | (u0 & c8) | c12);
+    }
+    *(uint4*)(Sc + d.o + 4 * lane) = make_uint4(out[0], out[1], out[2], out[3]);
+}
+
+// The chunk's 128 draws in stream order and each lane's four levels.
+template <int KIND>
+__device__ __forceinline__ void chunk_levels(uint32_t* B, StreamRegs& st, const StreamConst& k, const Cmp& cm,
+                                             int lane, uint32_t& lo4, uint32_t& hi4) {
+    uint32_t d[4];
+    if (KIND == ISG_RNG_MT19937) {
+        mt_quad<kAmscSlack>(B, st.iA, d, k.mul, lane);
+    } else if (KIND == ISG_RNG_PARISI_RAPUANO) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) d[j] = pr_warp_step(st.xA, st.xB, lane, 32);
+    } else {
+        d[0] = st.xA;
+        d[1] = st.xB;
+        d[2] = minstd_mulmod(st.xA, k.a64);
+        d[3] = minstd_mulmod(st.xB, k.a64);
+        st.xA = minstd_mulmod(d[2], k.a64);
+        st.xB = minstd_mulmod(d[3], k.a64);
+    }
+    uint32_t lo[4], hi[4];
+    const uint32_t dmin = min(min(d[0], d[1]), min(d[2], d[3]));
+    if (__any_sync(kFull, dmin < cm.c2)) {
+        level_ballots<4>(d, cm, lo, hi);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            lo[j] = __ballot_sync(kFull, d[j] < cm.c1);
+            hi[j] = 0u;
+        }
+    }
+    // site 4l + i of the chunk is bit 4(l & 7) + i of block l >> 3
+    const int jsel = lane >> 3, sh = 4 * (lane & 7);
+    const uint32_t lw = jsel == 0 ? lo[0] : (jsel == 1 ? lo[1] : (jsel == 2 ? lo[2] : lo[3]));
+    const uint32_t hw = jsel == 0 ? hi[0] : (jsel == 1 ? hi[1] : (jsel == 2 ? hi[2] : hi[3]));
+    lo4 = (lw >> sh) & 15u;
+    hi4 = (hw >> sh) & 15u;
+}
+
+__device__ __forceinline__ void chunk_process(const ChunkData& d, uint32_t* Sc, uint32_t lo4, uint32_t hi4, int lane) {
+    if (d.p == 0) chunk_update<0>(d, Sc, lo4, hi4, lane);
+    else chunk_update<1>(d, Sc, lo4, hi4, lane);
+}
+
+// Chunk n + 1's words are loaded (two buffers, A and B) before chunk n's draws
+// are made and its sites updated.
+template <int KIND>
+__global__ void __launch_bounds__(kAmscWarps * 32) amsc_chunk_kernel(AmscArgs a, FlipArgs gen, StreamConst k,
+                                                                     unsigned long long* tickets,
+                                                                     unsigned long long base) {
+    extern __shared__ uint32_t smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t* B = smem + wid * (KIND == ISG_RNG_MT19937 ? mt_window(kAmscSlack) : 0);
+    const AmscPtrs P = amsc_ptrs(a);
+    const Cmp cm{a.cmp1, a.cmp2, a.cmp3};
+    const int half = a.half, L = a.L;
+    for (;;) {
+        unsigned long long v = 0;
+        if (lane == 0) v = atomicAdd(tickets, 1ull);
+        v = __shfl_sync(kFull, v, 0);
+        const int64_t t = (int64_t)(v - base);
+        if (t >= a.S) break;
+        StreamRegs st;
+        load_stream<KIND>(gen, t, B, st, k, lane);
+        const int64_t r0 = t * a.R;
+        const int64_t r1 = r0 + a.R < a.rows ? r0 + a.R : a.rows;
+        const int64_t D = (r1 - r0) * half;
+        const int nch = (int)(D / kChunk);
+        RowCursor cur = cursor_at(a, r0);
+        ChunkData dA, dB;
+        chunk_load(P, chunk_offs(a, cur), lane, dA);
+        for (int n = 0; n < nch; n += 2) {
+            if (n + 1 < nch) {
+                cursor_next(cur, half, L);
+                chunk_load(P, chunk_offs(a, cur), lane, dB);
+            }
+            uint32_t lo4, hi4;
+            chunk_levels<KIND>(B, st, k, cm, lane, lo4, hi4);
+            chunk_process(dA, P.Sc, lo4, hi4, lane);
+            if (n + 1 >= nch) break;
+            if (n + 2 < nch) {
+                cursor_next(cur, half, L);
+                chunk_load(P, chunk_offs(a, cur), lane, dA);
+            }
+            chunk_levels<KIND>(B, st, k, cm, lane, lo4, hi4);
+            chunk_process(dB, P.Sc, lo4, hi4, lane);
+        }
+        if (KIND == ISG_RNG_MT19937) st.pos = (int)((st.pos + D) % kMtN);
+        store_stream<KIND>(gen, t, B, st, lane);
+    }
+}
+
 // Planes from the counter hash: bit b of the site word of sample b (Eq. 2).
 __global__ void amsc_init_kernel(uint32_t* planes, int64_t plane_words, int L, int half, AmscSeeds sd) {
     const int64_t rows = (int64_t)L * L;
@@ -324,9 +562,23 @@ static int amsc_occupancy(int kind, int deep, size_t smem) {
     });
 }
 
-// Sites in flight per lane that a sweep of this ensemble uses on the current
-// device: 8 with fewer than 16 streams per SM, else 4.
-static int amsc_depth(const isg_amsc* m) { return m->S < kAmscDeepStreamsPerSM * (int64_t)sm_count() ? 8 : 4; }
+// The sweep kernel's form for this ensemble on the current device: 0 = the
+// chunked form (rows of a multiple of 128 sites per colour), else the blocks
+// of 32 sites each lane keeps in flight in the site-strided form: 8 with fewer
+// than 16 streams per SM, 4 otherwise.
+static int amsc_form(const isg_amsc* m) {
+    if (m->half % kChunk == 0) return 0;
+    return m->S < kAmscDeepStreamsPerSM * (int64_t)sm_count() ? 8 : 4;
+}
+
+// Resident blocks per SM of the chunked kernel in registers.
+static int amsc_chunk_occupancy(int kind, size_t smem) {
+    return with_kind(kind, [&](auto kc) {
+        constexpr int K = decltype(kc)::value;
+        static std::atomic<int> cache[kDeviceSlots];
+        return occupancy_cached(cache, amsc_chunk_kernel<K>, kAmscWarps * 32, smem);
+    });
+}
 
 static unsigned amsc_grid(int64_t n, int threads, int64_t per_thread) {
     int64_t b = (n + threads - 1) / threads;
@@ -443,10 +695,11 @@ int isg_amsc_sweep(isg_amsc* m, int64_t n, void* cuda_stream) {
         a.cmp2 = (uint32_t)(((uint64_t)m->thr[2] + 1) / 2);
         a.cmp3 = (uint32_t)(((uint64_t)m->thr[3] + 1) / 2);
     }
-    const size_t smem = m->kind == ISG_RNG_MT19937 ? (size_t)kAmscWarps * mt_window(kAmscSlack) * 4 : 0;
     const int sms = sm_count();
-    const int deep = amsc_depth(m) == 8 ? 1 : 0;  // NB = 8: latency binds
-    const int oc = amsc_occupancy(m->kind, deep, smem);
+    const int form = amsc_form(m);
+    const bool chunked = form == 0, deep = form == 8;  // deep: NB = 8, latency binds
+    const size_t smem = m->kind == ISG_RNG_MT19937 ? (size_t)kAmscWarps * mt_window(kAmscSlack) * 4 : 0;
+    const int oc = chunked ? amsc_chunk_occupancy(m->kind, smem) : amsc_occupancy(m->kind, deep ? 1 : 0, smem);
     int64_t blocks = (int64_t)sms * oc;
     const int64_t need = (m->S + kAmscWarps - 1) / kAmscWarps;
     if (blocks > need) blocks = need;
@@ -454,12 +707,14 @@ int isg_amsc_sweep(isg_amsc* m, int64_t n, void* cuda_stream) {
         for (int c = 0; c < 2; ++c) {
             a.c = c;
             const cudaError_t e = with_kind(m->kind, [&](auto kc) {
-                if (deep)
-                    amsc_kernel<decltype(kc)::value, 8>
-                        <<<(unsigned)blocks, kAmscWarps * 32, smem, s>>>(a, gen, k, m->ctr, m->tickets);
+                constexpr int K = decltype(kc)::value;
+                if (chunked)
+                    amsc_chunk_kernel<K><<<(unsigned)blocks, kAmscWarps * 32, smem, s>>>(a, gen, k, m->ctr,
+                                                                                       m->tickets);
+                else if (deep)
+                    amsc_kernel<K, 8><<<(unsigned)blocks, kAmscWarps * 32, smem, s>>>(a, gen, k, m->ctr, m->tickets);
                 else
-                    amsc_kernel<decltype(kc)::value, 4>
-                        <<<(unsigned)blocks, kAmscWarps * 32, smem, s>>>(a, gen, k, m->ctr, m->tickets);
+                    amsc_kernel<K, 4><<<(unsigned)blocks, kAmscWarps * 32, smem, s>>>(a, gen, k, m->ctr, m->tickets);
                 return cudaGetLastError();
             });
             if (e != cudaSuccess) return cuda_fail(e, "isg_amsc_sweep");
@@ -470,12 +725,12 @@ int isg_amsc_sweep(isg_amsc* m, int64_t n, void* cuda_stream) {
     return ISG_OK;
 }
 
-int isg_amsc_info(const isg_amsc* m, int* L, int64_t* streams, int64_t* rows_per_stream, int* sites_in_flight) {
+int isg_amsc_info(const isg_amsc* m, int* L, int64_t* streams, int64_t* rows_per_stream, int* form) {
     if (!m) { set_error("isg_amsc_info: NULL handle"); return ISG_ERR_ARG; }
     if (L) *L = m->L;
     if (streams) *streams = m->S;
     if (rows_per_stream) *rows_per_stream = m->R;
-    if (sites_in_flight) *sites_in_flight = amsc_depth(m);
+    if (form) *form = amsc_form(m);
     return ISG_OK;
 }
 

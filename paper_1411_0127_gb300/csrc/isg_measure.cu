@@ -52,63 +52,93 @@ static unsigned grid_for(int64_t n, int threads) {
 }
 
 // ---------------------------------------------------------------- energy ---
-// Unsatisfied bonds of one word (the three forward bonds of its sites).
+// Thread t of a block owns word k = t % W of rows r = t / W + rows_per_block * j
+// (blocks striding over rows) and counts the forward bonds of that word in BOTH
+// colours, so every plane is read from memory once: the neighbour words of one
+// colour's word (rows y+1 and z+1 of the other colour, and the next word of the
+// row for the site whose +x neighbour is shifted) are words another thread of
+// the same pass reads as its own, found in L1 or L2.
 template <typename Word>
-struct UnsatIn {
-    Word s, nx, nx1, jx, jy, jz, ny, nz;
-    int k, p;
+struct UnsatPair {
+    Word s0, s1, jx0, jy0, jz0, jx1, jy1, jz1, n1y, n1z, n0y, n0z, nb;
+    int p0;
 };
 
 template <typename Word>
-__device__ __forceinline__ void unsat_load(const MeasGeom& g, unsigned q, unsigned rows, unsigned W, UnsatIn<Word>& u) {
-    const unsigned row = q / W;
-    u.k = (int)(q - row * W);
-    const int c = row >= rows ? 1 : 0;
-    const int r = (int)(row - (unsigned)c * rows);
-    const int L = g.L;
-    const int y = r % L, z = r / L;
-    u.p = (c + y + z) & 1;
-    const int yp = y == L - 1 ? 0 : y + 1, zp = z == L - 1 ? 0 : z + 1;
-    const size_t o = (size_t)r * W + u.k;
-    const Word* Sn = plane<Word>(g, c ^ 1, 0);
-    u.s = plane<Word>(g, c, 0)[o];
-    u.nx = Sn[o];
-    u.nx1 = u.p == 1 ? Sn[(size_t)r * W + (u.k == (int)W - 1 ? 0 : u.k + 1)] : Word(0);
-    u.jx = plane<Word>(g, c, 1)[o];
-    u.jy = plane<Word>(g, c, 2)[o];
-    u.jz = plane<Word>(g, c, 3)[o];
-    u.ny = Sn[(size_t)(yp + L * z) * W + u.k];
-    u.nz = Sn[(size_t)(y + L * zp) * W + u.k];
+__device__ __forceinline__ void unsat_pair_load(const MeasGeom& g, int r, int y, int z, int k, UnsatPair<Word>& u) {
+    const int L = g.L, W = g.W;
+    const size_t o = (size_t)r * W + k;
+    const int ryp = y == L - 1 ? r - (L - 1) : r + 1;
+    const int rzp = z == L - 1 ? r - (L - 1) * L : r + L;
+    const Word* S0 = plane<Word>(g, 0, 0);
+    const Word* S1 = plane<Word>(g, 1, 0);
+    u.p0 = (y + z) & 1;  // colour 0's row parity; colour 1's is the other
+    u.s0 = S0[o];
+    u.s1 = S1[o];
+    u.jx0 = plane<Word>(g, 0, 1)[o];
+    u.jy0 = plane<Word>(g, 0, 2)[o];
+    u.jz0 = plane<Word>(g, 0, 3)[o];
+    u.jx1 = plane<Word>(g, 1, 1)[o];
+    u.jy1 = plane<Word>(g, 1, 2)[o];
+    u.jz1 = plane<Word>(g, 1, 3)[o];
+    u.n1y = S1[(size_t)ryp * W + k];
+    u.n1z = S1[(size_t)rzp * W + k];
+    u.n0y = S0[(size_t)ryp * W + k];
+    u.n0z = S0[(size_t)rzp * W + k];
+    // the colour whose row parity is 1 has its +x neighbours shifted by one site
+    const size_t onb = (size_t)r * W + (k == W - 1 ? 0 : k + 1);
+    u.nb = (u.p0 == 1 ? S1 : S0)[onb];
 }
 
 template <typename Word>
-__device__ __forceinline__ int unsat_count(const MeasGeom& g, const UnsatIn<Word>& u) {
-    const Word nxp = u.p == 1 ? row_up<Word>(u.nx, u.nx1, u.k, g.W, g.nt) : u.nx;
-    const Word m = valid_mask<Word>(g, u.k);
-    return popcw((u.jx ^ u.s ^ nxp) & m) + popcw((u.jy ^ u.s ^ u.ny) & m) + popcw((u.jz ^ u.s ^ u.nz) & m);
+__device__ __forceinline__ int unsat_pair_count(const MeasGeom& g, int k, const UnsatPair<Word>& u) {
+    const Word m = valid_mask<Word>(g, k);
+    const Word nx0 = u.p0 == 1 ? row_up<Word>(u.s1, u.nb, k, g.W, g.nt) : u.s1;
+    const Word nx1 = u.p0 == 1 ? u.s0 : row_up<Word>(u.s0, u.nb, k, g.W, g.nt);
+    return popcw((u.jx0 ^ u.s0 ^ nx0) & m) + popcw((u.jy0 ^ u.s0 ^ u.n1y) & m) +
+           popcw((u.jz0 ^ u.s0 ^ u.n1z) & m) + popcw((u.jx1 ^ u.s1 ^ nx1) & m) +
+           popcw((u.jy1 ^ u.s1 ^ u.n0y) & m) + popcw((u.jz1 ^ u.s1 ^ u.n0z) & m);
 }
 
-// One thread per word of the two colours' planes, four words per iteration
-// with all their loads issued first.  The word count is below 2^31 for every
-// L <= 2048 (at most 2 * 2048^2 * 16), so the index arithmetic is 32-bit.
+// Rows advance by `step` per iteration: (y, z) follow with the precomputed
+// step % L and step / L and one carry.
+__device__ __forceinline__ void row_advance(int& r, int& y, int& z, int step, int sy, int sz, int L) {
+    r += step;
+    y += sy;
+    z += sz;
+    if (y >= L) {
+        y -= L;
+        ++z;
+    }
+}
+
 template <typename Word>
 __global__ void unsat_kernel(MeasGeom g, long long* out) {
-    const unsigned rows = (unsigned)g.rows, W = (unsigned)g.W;
-    const unsigned nw = 2u * rows * W;
-    const unsigned stride = gridDim.x * blockDim.x;
+    const int L = g.L, W = g.W, rows = (int)g.rows;
+    const int rpb = blockDim.x / W;  // rows per block and iteration
+    const int t = threadIdx.x;
+    const int rl = t / W, k = t - rl * W;
     long long acc = 0;
-    unsigned q = blockIdx.x * blockDim.x + threadIdx.x;
-    for (; q + 3 * stride < nw; q += 4 * stride) {
-        UnsatIn<Word> u[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) unsat_load(g, q + j * stride, rows, W, u[j]);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc += unsat_count(g, u[j]);
-    }
-    for (; q < nw; q += stride) {
-        UnsatIn<Word> u;
-        unsat_load(g, q, rows, W, u);
-        acc += unsat_count(g, u);
+    if (rl < rpb) {
+        const int step = gridDim.x * rpb;
+        const int sy = step % L, sz = step / L;
+        int r = blockIdx.x * rpb + rl;
+        int y = r % L, z = r / L;
+        // two rows in flight: all their loads are issued before either is counted
+        while (r < rows) {
+            int r2 = r, y2 = y, z2 = z;
+            row_advance(r2, y2, z2, step, sy, sz, L);
+            UnsatPair<Word> a, b;
+            unsat_pair_load<Word>(g, r, y, z, k, a);
+            const bool two = r2 < rows;
+            if (two) unsat_pair_load<Word>(g, r2, y2, z2, k, b);
+            acc += unsat_pair_count<Word>(g, k, a);
+            if (two) acc += unsat_pair_count<Word>(g, k, b);
+            r = r2;
+            y = y2;
+            z = z2;
+            row_advance(r, y, z, step, sy, sz, L);
+        }
     }
     for (int sh = 16; sh; sh >>= 1) acc += __shfl_xor_sync(kFull, acc, sh);
     if ((threadIdx.x & 31) == 0 && acc) atomicAdd((unsigned long long*)out, (unsigned long long)acc);
@@ -116,9 +146,13 @@ __global__ void unsat_kernel(MeasGeom g, long long* out) {
 
 cudaError_t launch_energy(const isg_sim* h, long long* out, cudaStream_t s) {
     const MeasGeom g = mgeom(h);
-    const int64_t nw = 2 * h->rows * h->W;
-    if (h->wbits == 64) unsat_kernel<uint64_t><<<grid_for(nw, 256), 256, 0, s>>>(g, out);
-    else unsat_kernel<uint32_t><<<grid_for(nw, 256), 256, 0, s>>>(g, out);
+    const int threads = 256;
+    const int64_t rpb = threads / h->W;
+    int64_t blocks = (h->rows + rpb - 1) / rpb;
+    const int64_t cap = (int64_t)sm_count() * 8;
+    if (blocks > cap) blocks = cap;
+    if (h->wbits == 64) unsat_kernel<uint64_t><<<(unsigned)blocks, threads, 0, s>>>(g, out);
+    else unsat_kernel<uint32_t><<<(unsigned)blocks, threads, 0, s>>>(g, out);
     return cudaGetLastError();
 }
 

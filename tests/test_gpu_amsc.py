@@ -8,8 +8,9 @@ and energies must agree bit for bit, every system, after every checked sweep.
 
 Sizes: L = 4 (two sites per row and colour), L = 10 and 50 (ragged tails of the
 32-site blocks), L = 50 and 64 (several streams), L = 256 (512 streams of 128
-rows), L = 432 and 512 (2456 and 4096 streams: the kernel form with four blocks
-of sites in flight per lane); beta = inf (only u >= 3 flips)."""
+rows; rows of 128 sites: the staged kernel form), L = 432 (2456 streams: the
+register form with four blocks of sites in flight per lane), L = 512 and 768
+(staged, two and three chunks per row); beta = inf (only u >= 3 flips)."""
 import math
 
 import numpy as np
@@ -50,6 +51,8 @@ def oracles(L, J, S, R, beta, kind):
     (64, "mt19937", 1 / 0.9, 3, 3),
     (10, "parisi_rapuano", 1 / 0.8, 6, 2),
     (50, "parisi_rapuano", 1 / 1.1, 4, 4),
+    (256, "minstd", 1 / 0.9, 2, 1),
+    (256, "parisi_rapuano", 1 / 0.7, 2, 2),
 ])
 def test_every_system_matches_its_lone_lattice(isg, L, kind, beta, sweeps, every):
     J, S = seeds(L)
@@ -92,14 +95,19 @@ def test_large_lattice_against_single_lattice_handles(isg):
         h.close()
 
 
-@pytest.mark.parametrize("L,kind,sweeps", [(432, "mt19937", 3), (512, "minstd", 2), (432, "parisi_rapuano", 2)])
-def test_bandwidth_form_against_lone_lattices_and_oracle(isg, L, kind, sweeps):
-    """The form of the sweep kernel that ensembles with at least 16 streams per
-    SM take (four blocks of 32 sites in flight per lane, the L = 1024
-    benchmark's form): all 32 energies against lone GPU handles seeded the same
-    way, the spins of systems 0, 13 and 31 against those handles, and system 5
-    directly against the oracle.  L = 432 has a 32-site tail block in every
-    stream (76 rows of 216 sites; the last stream 44 rows); L = 512 none."""
+@pytest.mark.parametrize("L,kind,sweeps,form", [
+    (432, "mt19937", 3, 4), (432, "parisi_rapuano", 2, 4),
+    (512, "minstd", 2, 0), (512, "parisi_rapuano", 2, 0), (768, "mt19937", 2, 0),
+])
+def test_large_ensembles_against_lone_lattices_and_oracle(isg, L, kind, sweeps, form):
+    """The kernel forms of large ensembles: the register form with four blocks
+    of 32 sites in flight per lane (at least 16 streams per SM and rows that are
+    not a multiple of 128 sites: L = 432, 2456 streams, a 32-site tail block in
+    every stream) and the staged form (rows of a multiple of 128 sites, fetched
+    by bulk copies: L = 512 with two chunks per row, L = 768 with three, so both
+    row wraps and interior chunks).  All 32 energies against lone GPU handles
+    seeded the same way, the spins of systems 0, 13 and 31 against those
+    handles, and system 5 directly against the oracle."""
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     beta = 1 / 0.9
@@ -107,8 +115,9 @@ def test_bandwidth_form_against_lone_lattices_and_oracle(isg, L, kind, sweeps):
     R = 0xA5C0 + L
     m = isg.Amsc(L, J, S, R, beta, kind)
     info = m.info()
-    assert info["streams"] >= 16 * sms, info
-    assert info["sites_in_flight"] == 4, info
+    assert info["form"] == form, info
+    if form == 4:
+        assert info["streams"] >= 16 * sms, info
     m.sweep(sweeps)
     E = m.energies()
     for b in range(32):
