@@ -202,21 +202,29 @@ int isg_batch_create(int n, const int *L, const uint64_t *seed_J, const uint64_t
 void isg_batch_destroy(isg_batch *b);
 
 /* Number of samples, of work bundles (streams of small lattices packed 32 per
- * bundle) and of spin-flip attempts per sweep of the whole batch. */
+ * bundle; with the pass engine, shape 4: the (lattice, stream) items) and of
+ * spin-flip attempts per sweep of the whole batch. */
 int isg_batch_info(const isg_batch *b, int *samples, int *bundles, int64_t *attempts_per_sweep);
 
-/* Execution configuration of the batch's persistent launches, the space the
- * autotuner (paper_1411_0127_gb300/autotune.py) searches.  No configuration
- * changes a result: every replica follows its own trajectory whatever the
- * bundles, so all of them give bit-identical states.
+/* Execution configuration of the batch's launches, the space the autotuner
+ * (paper_1411_0127_gb300/autotune.py) searches.  No configuration changes a
+ * result: every replica follows its own trajectory whatever the bundles, so
+ * all of them give bit-identical states.  Replicas keep their spins and
+ * couplings in 64-bit words whatever L.
  *   shape     CTA shape: 0 = one CTA of 32 warps per SM, 1 = one of 24,
- *             2 = one of 16, 3 = two of 16 (the "tile": warps sweeping a bundle)
+ *             2 = one of 16, 3 = two of 16 (the "tile": warps sweeping a bundle),
+ *             all persistent over a whole sweep group; 4 = the pass engine: no
+ *             bundles, each colour pass of all replicas is one launch of 4-warp
+ *             CTAs taking (lattice, stream) items by ticket, longest first (the
+ *             group's launches are captured into one graph; capacity and
+ *             resident do not apply, every stream's state is loaded and stored
+ *             around each pass)
  *   capacity  streams per packed bundle of small lattices, 1 .. warps of the
  *             shape; 0 = the shape's warps
  *   resident  1: the generator state of a bundle that fits in the CTA stays in
  *             shared memory / registers for a whole launch; 0: it is loaded and
  *             stored around every colour pass
- *   words_per_lane  32-bit words of a row group each lane updates, 1 or 2
+ *   words_per_lane  words of a row group each lane updates, 1 or 2
  *             (a row group is 32 * words_per_lane words: its draws are made in
  *             one run, and 2 halves the groups per pass)
  * Synchronises the device, re-plans the bundles and drops the captured graph;

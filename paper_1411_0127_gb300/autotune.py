@@ -1,7 +1,8 @@
 """Autotuner of the batched persistent engine.
 
-The batch kernel's execution configuration (isg_batch_set_config: CTA shape,
-streams per bundle, generator-state placement, words per lane) changes its speed but never its
+The batch's execution configuration (isg_batch_set_config: CTA shape of the
+persistent bundle kernel or the per-pass engine, streams per bundle,
+generator-state placement, words per lane) changes its speed but never its
 results, so the tuner can pick it by measurement alone.  It times every
 candidate on a twin of the batch (same samples, seeds and temperatures, a
 separate copy of the state), so the batch's own trajectories are not touched,
@@ -16,6 +17,7 @@ import os
 
 # (shape, capacity, resident, words per lane); see isg_batch_set_config
 SHAPE_WARPS = {0: 32, 1: 24, 2: 16, 3: 16}
+PASS_SHAPE = 4          # the pass engine: one launch per colour pass, no bundles
 
 
 def candidates() -> list:
@@ -25,6 +27,8 @@ def candidates() -> list:
             for resident in (1, 0):
                 for wpt in (1, 2):
                     out.append((shape, cap, resident, wpt))
+    for wpt in (1, 2):           # capacity and resident do not apply to it
+        out.append((PASS_SHAPE, 4, 0, wpt))
     return out
 
 

@@ -90,7 +90,9 @@ static bool beta_ok(double beta) { return beta > 0.0; }  // false for 0, negativ
 static int alloc_sim(isg_sim* h) {
     h->half = h->L / 2;
     const int w64 = (h->half + 63) / 64, w32 = (h->half + 31) / 32;
-    h->wbits = (2 * w64 == w32 && !h->force32) ? 64 : 32;
+    // 64-bit words where they waste no more bits than 32-bit ones; batch members
+    // always use them (one kernel instantiation serves every size of a batch)
+    h->wbits = (h->member || 2 * w64 == w32) ? 64 : 32;
     h->W = (h->half + h->wbits - 1) / h->wbits;
     h->nt = h->half - (h->W - 1) * h->wbits;
     h->rows = (int64_t)h->L * h->L;
@@ -169,7 +171,7 @@ static int restart_tracking(isg_sim* h, cudaStream_t s) {
     return e == cudaSuccess ? ISG_OK : cuda_fail(e, "reset tracked energy");
 }
 
-int create_sim(int L, uint64_t seed_J, uint64_t seed_spin, uint64_t seed_rng, double beta, int rng_kind, bool force32,
+int create_sim(int L, uint64_t seed_J, uint64_t seed_spin, uint64_t seed_rng, double beta, int rng_kind, bool member,
                isg_sim** out) {
     if (!out) { set_error("isg_create: out is NULL"); return ISG_ERR_ARG; }
     *out = nullptr;
@@ -187,7 +189,7 @@ int create_sim(int L, uint64_t seed_J, uint64_t seed_spin, uint64_t seed_rng, do
     h->seed_J = seed_J;
     h->seed_spin = seed_spin;
     h->seed_rng = seed_rng;
-    h->force32 = force32;
+    h->member = member;
     thresholds(beta, h->thr);
     int rc = alloc_sim(h);
     if (rc) { free_sim(h); return rc; }
@@ -203,10 +205,10 @@ int create_sim(int L, uint64_t seed_J, uint64_t seed_spin, uint64_t seed_rng, do
 void destroy_sim(isg_sim* h) { free_sim(h); }
 
 // Device bytes a handle of this size and kind holds (planes, streams, words).
-size_t sim_device_bytes(int L, int rng_kind, bool force32) {
+size_t sim_device_bytes(int L, int rng_kind, bool member) {
     const int half = L / 2;
     const int w64 = (half + 63) / 64, w32 = (half + 31) / 32;
-    const int wbits = (2 * w64 == w32 && !force32) ? 64 : 32;
+    const int wbits = (member || 2 * w64 == w32) ? 64 : 32;
     const int W = (half + wbits - 1) / wbits;
     const int64_t rows = (int64_t)L * L;
     int64_t R = 0, S = 0;
@@ -582,9 +584,9 @@ int isg_load(const void* buf, size_t n, isg_sim** out) {
     h->seed_spin = hd.seed_spin;
     h->seed_rng = hd.seed_rng;
     {
-        // 32-bit words where 64-bit ones would be chosen: the saved handle had them forced
+        // 64-bit words where 32-bit ones would be chosen: the saved handle was a batch member
         const int half = h->L / 2, w64 = (half + 63) / 64, w32 = (half + 31) / 32;
-        h->force32 = hd.wbits == 32 && 2 * w64 == w32;
+        h->member = hd.wbits == 64 && 2 * w64 != w32;
     }
     thresholds(h->beta, h->thr);
     int rc = alloc_sim(h);

@@ -3,7 +3,7 @@
 //
 // The paper fills the GPU with many samples at once (Sec. 2, coded samples k;
 // Sec. 4 results, psFlip against k).  Here a batch is a set of ordinary
-// lattices (32-bit words forced, so one kernel template serves every L), two
+// lattices (64-bit words whatever L, so one kernel template serves every L), two
 // per sample with the same couplings and different spin seeds, and:
 //   * on the host their RNG streams are packed into bundles: a lattice with more
 //     than `capacity` streams is one bundle; smaller lattices are packed
@@ -43,7 +43,8 @@ struct isg_batch {
     int* d_boff = nullptr;              // bundle offsets into d_entries
     unsigned* d_ctr = nullptr;          // [0] next task, [1] CTAs done, [2] dependency-wait error
     isg::BundleTasks tasks;             // launch order of the bundles, long ones split in two
-    int nbundles = 0;
+    int nbundles = 0;                   // bundles, or (pass engine) items
+    int2* d_items = nullptr;            // pass engine: (lattice, stream), longest streams first
     int64_t attempts_per_sweep = 0;
     isg::BundleConfig cfg;              // execution configuration (isg_batch_set_config)
     cudaStream_t cap = nullptr;         // private stream used for graph capture
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(WARPS * 32, PER_SM) batch_kernel(BatchArgs b, 
                 a.cmp3 = g.cmp3;
                 int dE = 0;
                 const int64_t rb = (int64_t)e.y * g.R, re = rb + g.R < g.rows ? rb + g.R : g.rows;
-                stream_pass<uint32_t, KIND, kBatchSlack, true, WPT>(a, pass & 1, rb, re, ring, cond, st, k, lane, dE);
+                stream_pass<uint64_t, KIND, kBatchSlack, true, WPT>(a, pass & 1, rb, re, ring, cond, st, k, lane, dE);
                 if (!resident) store_stream<KIND>(g, e.y, ring, st, lane);
                 for (int sh = 16; sh; sh >>= 1) dE += __shfl_xor_sync(kFull, dE, sh);
                 if (lane == 0 && dE != 0) atomicAdd((unsigned long long*)g.dE, (unsigned long long)(long long)dE);
@@ -248,7 +249,95 @@ cudaError_t launch_bundle_kernel(int kind, const BundleConfig& cfg, const FlipAr
     });
 }
 
-int bundle_warps(const BundleConfig& cfg) { return kBundleShapes[cfg.shape].warps; }
+int bundle_warps(const BundleConfig& cfg) { return cfg.shape == kPassShape ? 4 : kBundleShapes[cfg.shape].warps; }
+
+// ---------------------------------------------------------------------------
+// Pass engine (shape kPassShape): no bundles and no block barriers.  Every
+// colour pass of all the batch's lattices is one launch of persistent 4-warp
+// CTAs, as many as fit, whose warps take (lattice, stream) items by ticket,
+// longest streams first; a warp loads the stream's generator state, sweeps the
+// stream's rows with the same stream_pass as the single-lattice kernel
+// (throughput form) and stores the state back.  The last CTA to leave returns
+// the ticket counter to zero, so the launches of a sweep group are captured
+// into one graph and replayed.
+constexpr int kPassWarps = 4;
+constexpr int kPassSlack = 1024;
+
+template <int KIND, int WPT>
+__global__ void __launch_bounds__(kPassWarps * 32, 7)
+    pass_kernel(const FlipArgs* reps, const int2* items, int nitems, int c, unsigned* ctr, StreamConst k) {
+    extern __shared__ uint32_t smem[];
+    constexpr int kRing = KIND == ISG_RNG_MT19937 ? mt_window(kPassSlack) : 0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t* ring = smem + wid * (kRing + 2 * WPT * kCondWords);
+    uint32_t* cond = ring + kRing;
+    for (;;) {
+        unsigned v = 0;
+        if (lane == 0) v = atomicAdd(&ctr[0], 1u);
+        v = __shfl_sync(kFull, v, 0);
+        if (v >= (unsigned)nitems) break;
+        const int2 e = items[v];
+        const FlipArgs& g = reps[e.x];
+        FlipArgs a;  // the fields stream_pass reads, in registers
+        a.planes = g.planes;
+        a.plane_bytes = g.plane_bytes;
+        a.L = g.L;
+        a.half = g.half;
+        a.W = g.W;
+        a.nt = g.nt;
+        a.cmp1 = g.cmp1;
+        a.cmp2 = g.cmp2;
+        a.cmp3 = g.cmp3;
+        StreamRegs st;
+        load_stream<KIND>(g, e.y, ring, st, k, lane);
+        int dE = 0;
+        const int64_t rb = (int64_t)e.y * g.R, re = rb + g.R < g.rows ? rb + g.R : g.rows;
+        stream_pass<uint64_t, KIND, kPassSlack, true, WPT>(a, c, rb, re, ring, cond, st, k, lane, dE);
+        store_stream<KIND>(g, e.y, ring, st, lane);
+        for (int sh = 16; sh; sh >>= 1) dE += __shfl_xor_sync(kFull, dE, sh);
+        if (lane == 0 && dE != 0) atomicAdd((unsigned long long*)g.dE, (unsigned long long)(long long)dE);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned done = atomicAdd(&ctr[1], 1u);
+        if (done == gridDim.x - 1) {
+            atomicExch(&ctr[0], 0u);
+            atomicExch(&ctr[1], 0u);
+            __threadfence();
+        }
+    }
+}
+
+static size_t pass_smem(int kind, int wpt) {
+    const int ring = kind == ISG_RNG_MT19937 ? mt_window(kPassSlack) : 0;
+    return (size_t)kPassWarps * (ring + 2 * wpt * kCondWords) * sizeof(uint32_t);
+}
+
+// Colour passes of `sweeps` sweeps of every lattice: 2 * sweeps launches.
+static cudaError_t launch_passes(int kind, int wpt, const FlipArgs* reps, const int2* items, int nitems, int sweeps,
+                                 unsigned* ctr, cudaStream_t s) {
+    if (nitems <= 0 || sweeps <= 0) return cudaSuccess;
+    const StreamConst k = stream_const();
+    const size_t smem = pass_smem(kind, wpt);
+    return with_kind(kind, [&](auto kc) {
+        return with_wpt(wpt, [&](auto wc) {
+            constexpr int K = decltype(kc)::value, WPT = decltype(wc)::value;
+            static std::atomic<int> occ_cache[kDeviceSlots];
+            const int occ = occupancy_cached(occ_cache, pass_kernel<K, WPT>, kPassWarps * 32, smem);
+            int64_t grid = (int64_t)sm_count() * occ;
+            const int64_t need = (nitems + kPassWarps - 1) / kPassWarps;
+            if (grid > need) grid = need;
+            for (int sw = 0; sw < sweeps; ++sw)
+                for (int c = 0; c < 2; ++c) {
+                    pass_kernel<K, WPT><<<(unsigned)grid, kPassWarps * 32, smem, s>>>(reps, items, nitems, c, ctr, k);
+                    const cudaError_t e = cudaGetLastError();
+                    if (e != cudaSuccess) return e;
+                }
+            return cudaSuccess;
+        });
+    });
+}
 
 void plan_bundles(const std::vector<isg_sim*>& reps, std::vector<int2>& entries, std::vector<int>& boff,
                   std::vector<int>* order, int capacity) {
@@ -305,6 +394,8 @@ void plan_bundles(const std::vector<isg_sim*>& reps, std::vector<int2>& entries,
 }
 
 static cudaError_t batch_launch(isg_batch* b, int sweeps, cudaStream_t s) {
+    if (b->cfg.shape == kPassShape)
+        return launch_passes(b->kind, b->cfg.wpt, b->d_reps, b->d_items, b->nbundles, sweeps, b->d_ctr, s);
     return launch_bundle_kernel(b->kind, b->cfg, b->d_reps, b->d_entries, b->d_boff, nullptr, b->nbundles, sweeps,
                                 b->d_ctr, s, &b->tasks);
 }
@@ -356,13 +447,36 @@ static std::vector<int4> split_tasks(const isg_batch* b, const std::vector<int2>
 // Bundles for the configuration's capacity, uploaded (the entries keep their
 // number; the offsets are reallocated); the captured graph is dropped.
 static int batch_plan(isg_batch* b) {
-    std::vector<int2> entries;
-    std::vector<int> boff;
-    plan_bundles(b->reps, entries, boff, nullptr, b->cfg.capacity);
     isg_sim* h0 = b->reps[0];
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
     if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
     b->graph_group = 0;
+    if (b->cfg.shape == kPassShape) {
+        // every stream of every lattice is an item; the longest go first
+        std::vector<int2> items;
+        std::vector<int64_t> len;
+        for (int r = 0; r < (int)b->reps.size(); ++r) {
+            const isg_sim* h = b->reps[r];
+            for (int64_t t = 0; t < h->S; ++t) items.push_back(make_int2(r, (int)t));
+        }
+        auto draws = [&](const int2& it) {
+            const isg_sim* h = b->reps[it.x];
+            const int64_t r0 = (int64_t)it.y * h->R, r1 = std::min(r0 + h->R, h->rows);
+            return (r1 - r0) * h->half;
+        };
+        std::stable_sort(items.begin(), items.end(), [&](const int2& x, const int2& y) { return draws(x) > draws(y); });
+        if (!b->d_items) b->d_items = (int2*)dev_alloc(h0, items.size() * sizeof(int2));
+        if (!b->d_items) {
+            set_error("isg_batch: device allocation failed");
+            return ISG_ERR_NOMEM;
+        }
+        b->nbundles = (int)items.size();
+        const cudaError_t e = cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice);
+        return e == cudaSuccess ? ISG_OK : cuda_fail(e, "isg_batch: pass plan");
+    }
+    std::vector<int2> entries;
+    std::vector<int> boff;
+    plan_bundles(b->reps, entries, boff, nullptr, b->cfg.capacity);
     dev_free(h0, b->d_boff);
     b->d_boff = (int*)dev_alloc(h0, boff.size() * sizeof(int));
     if (!b->d_entries) b->d_entries = (int2*)dev_alloc(h0, entries.size() * sizeof(int2));
@@ -405,6 +519,7 @@ static void batch_free(isg_batch* b) {
         dev_free(b->reps[0], b->d_ctr);
         dev_free(b->reps[0], b->tasks.d_tasks);
         dev_free(b->reps[0], b->tasks.d_done);
+        dev_free(b->reps[0], b->d_items);
     }
     for (isg_sim* h : b->reps) destroy_sim(h);
     delete b;
@@ -483,7 +598,7 @@ int isg_batch_info(const isg_batch* b, int* samples, int* bundles, int64_t* atte
 }
 
 int isg_batch_set_config(isg_batch* b, int shape, int capacity, int resident, int words_per_lane) {
-    if (!b || shape < 0 || shape >= kBundleShapeCount || capacity < 0 || (resident != 0 && resident != 1) ||
+    if (!b || shape < 0 || shape > kPassShape || capacity < 0 || (resident != 0 && resident != 1) ||
         (words_per_lane != 1 && words_per_lane != 2)) {
         set_error("isg_batch_set_config: bad argument");
         return ISG_ERR_ARG;
@@ -515,6 +630,7 @@ int isg_batch_get_config(const isg_batch* b, int* shape, int* capacity, int* res
 
 int isg_batch_test_stall(isg_batch* b) {
     if (!b) { set_error("isg_batch_test_stall: NULL batch"); return ISG_ERR_ARG; }
+    if (b->cfg.shape == kPassShape) { set_error("isg_batch_test_stall: the pass engine has no tasks"); return ISG_ERR_STATE; }
     const int n = b->tasks.ntasks;
     if (n < 2) { set_error("isg_batch_test_stall: fewer than two tasks"); return ISG_ERR_STATE; }
     int4 t;

@@ -11,7 +11,9 @@ namespace isg {
 // Execution configuration of the persistent bundle kernel.  None of it changes
 // a result: every lattice follows its own trajectory whatever the bundles.
 //   shape     0: one CTA of 32 warps per SM, 1: one of 24, 2: one of 16,
-//             3: two of 16
+//             3: two of 16; kPassShape (batches only): no bundles, every colour
+//             pass of all lattices is one launch whose warps take (lattice,
+//             stream) items by ticket (capacity and resident do not apply)
 //   capacity  streams per packed bundle of small lattices (1 .. warps of the shape)
 //   resident  1: the generator state of a bundle that fits in the CTA stays in
 //             shared memory / registers for the whole launch; 0: it is loaded
@@ -19,6 +21,7 @@ namespace isg {
 //   wpt       words of a row group each lane updates (1 or 2): a row group is
 //             wpt * 32 words, so 2 halves the groups per pass
 constexpr int kBundleShapeCount = 4;
+constexpr int kPassShape = 4;
 struct BundleConfig {
     int shape = 0;
     int capacity = 32;

@@ -250,7 +250,8 @@ __device__ __forceinline__ Word row_down(Word cur, Word nb, int k, int nt) {
 // The opaque handle.
 struct isg_sim {
     int L = 0, half = 0, wbits = 0, W = 0, nt = 0;
-    bool force32 = false;               // 32-bit words whatever L (batch members)
+    bool member = false;                // batch member or batched server job: 64-bit words whatever L,
+                                        // no segmented streams
     int kind = 0;
     double beta = 0.0;
     uint32_t thr[4] = {0, 0, 0, 0};
@@ -306,10 +307,10 @@ void set_error(const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
 void* dev_alloc(isg_sim* h, size_t n);
 void dev_free(isg_sim* h, void* p);
-int create_sim(int L, uint64_t seed_J, uint64_t seed_spin, uint64_t seed_rng, double beta, int rng_kind, bool force32,
+int create_sim(int L, uint64_t seed_J, uint64_t seed_spin, uint64_t seed_rng, double beta, int rng_kind, bool member,
                isg_sim** out);
 void destroy_sim(isg_sim* h);
-size_t sim_device_bytes(int L, int rng_kind, bool force32);
+size_t sim_device_bytes(int L, int rng_kind, bool member);
 // floor(2^32 exp(-4 k beta)) for k = 1..3, thr[0] = 0 (Sec. 4)
 void thresholds(double beta, uint32_t thr[4]);
 

@@ -130,14 +130,14 @@ static uint32_t minstd_pow(uint32_t a, uint64_t e) {
 
 // Segments of a MINSTD launch with fewer streams than the resident warps can
 // take (nseg = 1 otherwise): about two items per resident warp, each at least
-// one row group.  Not for batch members and batched server jobs (force32): their
+// one row group.  Not for batch members and batched server jobs (member): their
 // state pointers are also held in device descriptors and captured graphs, which
 // the buffer swap would leave behind.
 static Segments plan_segments(const isg_sim* h, int64_t resident_warps, bool latency_form) {
     Segments sg;
     memset(&sg, 0, sizeof sg);
     sg.nseg = 1;
-    if (h->kind != ISG_RNG_MINSTD || !latency_form || !h->rng_alt || h->force32) return sg;
+    if (h->kind != ISG_RNG_MINSTD || !latency_form || !h->rng_alt || h->member) return sg;
     const int64_t G = 32 / h->W;
     const int64_t groups = (h->R + G - 1) / G;
     int64_t nseg = (2 * resident_warps + h->S - 1) / h->S;

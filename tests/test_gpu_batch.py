@@ -206,7 +206,8 @@ def test_autotuner_picks_a_candidate_and_caches_it(isg, tmp_path):
 def test_batch_config_rejects_bad_values(isg):
     L, J, S, B = mixed()
     b = isg.Batch(L[:2], J[:2], S[:4], B[:2], "minstd")
-    for bad in [(4, 0, 1, 1), (-1, 0, 1, 1), (2, 17, 1, 1), (0, 33, 1, 1), (0, 8, 2, 1), (0, 8, 1, 3), (0, 8, 1, 0)]:
+    for bad in [(5, 0, 1, 1), (-1, 0, 1, 1), (2, 17, 1, 1), (0, 33, 1, 1), (0, 8, 2, 1), (0, 8, 1, 3), (0, 8, 1, 0),
+                (4, 5, 0, 1)]:
         with pytest.raises(isg.IsgError):
             b.set_config(*bad)
     assert b.get_config() == (0, 32, 1, 1)
