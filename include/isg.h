@@ -202,7 +202,7 @@ int isg_batch_create(int n, const int *L, const uint64_t *seed_J, const uint64_t
 void isg_batch_destroy(isg_batch *b);
 
 /* Number of samples, of work bundles (streams of small lattices packed 32 per
- * bundle; with the pass engine, shape 4: the (lattice, stream) items) and of
+ * bundle; with the pass engines, shapes 4 and 5: the (lattice, stream) items) and of
  * spin-flip attempts per sweep of the whole batch. */
 int isg_batch_info(const isg_batch *b, int *samples, int *bundles, int64_t *attempts_per_sweep);
 
@@ -213,12 +213,14 @@ int isg_batch_info(const isg_batch *b, int *samples, int *bundles, int64_t *atte
  * couplings in 64-bit words whatever L.
  *   shape     CTA shape: 0 = one CTA of 32 warps per SM, 1 = one of 24,
  *             2 = one of 16, 3 = two of 16 (the "tile": warps sweeping a bundle),
- *             all persistent over a whole sweep group; 4 = the pass engine: no
- *             bundles, each colour pass of all replicas is one launch of 4-warp
- *             CTAs taking (lattice, stream) items by ticket, longest first (the
- *             group's launches are captured into one graph; capacity and
- *             resident do not apply, every stream's state is loaded and stored
- *             around each pass)
+ *             all persistent over a whole sweep group; 4 and 5 = the pass
+ *             engines, no bundles: 4-warp CTAs take (lattice, stream) items of
+ *             a colour pass by ticket, longest streams first; with 4 each
+ *             colour pass of all replicas is one launch, with 5 one persistent
+ *             launch per sweep group takes the items pass by pass and an item
+ *             waits (bounded) only until its own lattice has finished the
+ *             previous pass (capacity and resident do not apply to 4 and 5:
+ *             every stream's state is loaded and stored around each pass)
  *   capacity  streams per packed bundle of small lattices, 1 .. warps of the
  *             shape; 0 = the shape's warps
  *   resident  1: the generator state of a bundle that fits in the CTA stays in
@@ -402,10 +404,13 @@ int isg_stencil_decisions(const uint16_t *code, const uint32_t *draw, int64_t n,
  * position, without advancing it (sync); host_out gets the 32-bit draws. */
 int isg_peek_draws(const isg_sim *h, int64_t t, int64_t n, uint32_t *host_out);
 
-/* Make the last task of the batch's launches wait for itself, a flag that
- * nothing sets, so that its bounded wait runs out (about 4 s per launch) and
- * the error path can be tested.  The next isg_batch_set_config restores the
- * plan.  ISG_ERR_STATE if the batch has fewer than two tasks. */
+/* Make one wait of the batch's launches wait for something that never comes,
+ * so that its bounded wait runs out (about 4 s per launch) and the error path
+ * can be tested: with the bundle shapes, the last task waits for its own done
+ * flag; with the group pass engine (shape 5), the pass-1 items of the lattice
+ * with the fewest streams wait for one completed item too many.  The next
+ * isg_batch_set_config restores the plan.  ISG_ERR_STATE with shape 4 (its
+ * launches have no waits) or if a bundle plan has fewer than two tasks. */
 int isg_batch_test_stall(isg_batch *b);
 
 #ifdef __cplusplus

@@ -17,7 +17,7 @@ import os
 
 # (shape, capacity, resident, words per lane); see isg_batch_set_config
 SHAPE_WARPS = {0: 32, 1: 24, 2: 16, 3: 16}
-PASS_SHAPE = 4          # the pass engine: one launch per colour pass, no bundles
+PASS_SHAPES = (4, 5)    # the pass engines: one launch per colour pass / per sweep group, no bundles
 
 
 def candidates() -> list:
@@ -27,8 +27,9 @@ def candidates() -> list:
             for resident in (1, 0):
                 for wpt in (1, 2):
                     out.append((shape, cap, resident, wpt))
-    for wpt in (1, 2):           # capacity and resident do not apply to it
-        out.append((PASS_SHAPE, 4, 0, wpt))
+    for shape in PASS_SHAPES:    # capacity and resident do not apply to them
+        for wpt in (1, 2):
+            out.append((shape, 4, 0, wpt))
     return out
 
 

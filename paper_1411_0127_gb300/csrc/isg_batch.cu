@@ -45,6 +45,8 @@ struct isg_batch {
     isg::BundleTasks tasks;             // launch order of the bundles, long ones split in two
     int nbundles = 0;                   // bundles, or (pass engine) items
     int2* d_items = nullptr;            // pass engine: (lattice, stream), longest streams first
+    unsigned* d_done = nullptr;         // pass engine: per lattice, items completed in the running launch
+    int stall = -1;                     // pass engine test hook (isg_batch_test_stall)
     int64_t attempts_per_sweep = 0;
     isg::BundleConfig cfg;              // execution configuration (isg_batch_set_config)
     cudaStream_t cap = nullptr;         // private stream used for graph capture
@@ -249,35 +251,76 @@ cudaError_t launch_bundle_kernel(int kind, const BundleConfig& cfg, const FlipAr
     });
 }
 
-int bundle_warps(const BundleConfig& cfg) { return cfg.shape == kPassShape ? 4 : kBundleShapes[cfg.shape].warps; }
+int bundle_warps(const BundleConfig& cfg) { return cfg.shape >= kPassShape ? 4 : kBundleShapes[cfg.shape].warps; }
 
 // ---------------------------------------------------------------------------
-// Pass engine (shape kPassShape): no bundles and no block barriers.  Every
-// colour pass of all the batch's lattices is one launch of persistent 4-warp
-// CTAs, as many as fit, whose warps take (lattice, stream) items by ticket,
-// longest streams first; a warp loads the stream's generator state, sweeps the
-// stream's rows with the same stream_pass as the single-lattice kernel
-// (throughput form) and stores the state back.  The last CTA to leave returns
-// the ticket counter to zero, so the launches of a sweep group are captured
-// into one graph and replayed.
+// Pass engines (shapes kPassShape and kGroupShape): no bundles and no block
+// barriers.  Persistent 4-warp CTAs take items by ticket, longest streams
+// first; an item is one stream of one lattice in one colour pass: a warp loads
+// the stream's generator state, sweeps the stream's rows with the same
+// stream_pass as the single-lattice kernel (throughput form) and stores the
+// state back.  With kPassShape every colour pass is one launch.  With
+// kGroupShape one launch runs all the passes of a sweep group, items taken pass
+// by pass: a lattice's pass p reads the spins and continues the generator
+// states its pass p - 1 left, so an item of pass p first waits (bounded) until
+// its lattice has completed all items of the earlier passes (a per-lattice
+// count); other lattices need not wait, so passes overlap across lattices.
+// Items are taken in pass order, so every item waited for is already held by a
+// running warp: the waits always end.  The last CTA to leave returns the
+// ticket counter (and the lattice counts) to zero, so the launches are
+// captured once into a CUDA graph and replayed.
 constexpr int kPassWarps = 4;
 constexpr int kPassSlack = 1024;
 
-template <int KIND, int WPT>
-__global__ void __launch_bounds__(kPassWarps * 32, 7)
-    pass_kernel(const FlipArgs* reps, const int2* items, int nitems, int c, unsigned* ctr, StreamConst k) {
+struct PassArgs {
+    const FlipArgs* reps;
+    const int2* items;   // (lattice, stream), longest streams first
+    int nitems;
+    int npasses;         // passes of this launch (1 for a launch per pass)
+    int c0;              // colour of its first pass
+    int nlat;
+    int stall;           // test hook: this lattice's pass-1 items wait for one item too many (-1: none)
+    unsigned* ctr;       // [0] next ticket, [1] CTAs done, [2] sticky error: a wait gave up
+    unsigned* done;      // per lattice: items completed in this launch
+};
+
+template <int KIND, int WPT, bool GROUP>
+__global__ void __launch_bounds__(kPassWarps * 32, 7) pass_kernel(PassArgs pa, StreamConst k) {
     extern __shared__ uint32_t smem[];
     constexpr int kRing = KIND == ISG_RNG_MT19937 ? mt_window(kPassSlack) : 0;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint32_t* ring = smem + wid * (kRing + 2 * WPT * kCondWords);
     uint32_t* cond = ring + kRing;
+    const unsigned total = (unsigned)pa.npasses * (unsigned)pa.nitems;
     for (;;) {
         unsigned v = 0;
-        if (lane == 0) v = atomicAdd(&ctr[0], 1u);
+        if (lane == 0) v = atomicAdd(&pa.ctr[0], 1u);
         v = __shfl_sync(kFull, v, 0);
-        if (v >= (unsigned)nitems) break;
-        const int2 e = items[v];
-        const FlipArgs& g = reps[e.x];
+        if (v >= total) break;
+        const int p = GROUP ? (int)(v / (unsigned)pa.nitems) : 0;
+        const int2 e = pa.items[v - (unsigned)p * (unsigned)pa.nitems];
+        const FlipArgs& g = pa.reps[e.x];
+        if (GROUP && p > 0) {
+            const unsigned need = (unsigned)p * (unsigned)g.S + (e.x == pa.stall && p == 1 ? 1u : 0u);
+            int ok = 1;
+            if (lane == 0) {
+                ok = 0;
+                for (int it = 0; it < kDepWaitLimit; ++it) {
+                    if (*(volatile const unsigned*)(pa.done + e.x) >= need) {
+                        ok = 1;
+                        break;
+                    }
+                    __nanosleep(256);
+                }
+                if (!ok) atomicExch(&pa.ctr[2], 1u);
+            }
+            ok = __shfl_sync(kFull, ok, 0);
+            __threadfence();
+            if (!ok) {  // counted but not swept: the error is reported, and nothing waits on it forever
+                if (lane == 0) atomicAdd(pa.done + e.x, 1u);
+                continue;
+            }
+        }
         FlipArgs a;  // the fields stream_pass reads, in registers
         a.planes = g.planes;
         a.plane_bytes = g.plane_bytes;
@@ -292,18 +335,24 @@ __global__ void __launch_bounds__(kPassWarps * 32, 7)
         load_stream<KIND>(g, e.y, ring, st, k, lane);
         int dE = 0;
         const int64_t rb = (int64_t)e.y * g.R, re = rb + g.R < g.rows ? rb + g.R : g.rows;
-        stream_pass<uint64_t, KIND, kPassSlack, true, WPT>(a, c, rb, re, ring, cond, st, k, lane, dE);
+        stream_pass<uint64_t, KIND, kPassSlack, true, WPT>(a, (pa.c0 + p) & 1, rb, re, ring, cond, st, k, lane, dE);
         store_stream<KIND>(g, e.y, ring, st, lane);
         for (int sh = 16; sh; sh >>= 1) dE += __shfl_xor_sync(kFull, dE, sh);
         if (lane == 0 && dE != 0) atomicAdd((unsigned long long*)g.dE, (unsigned long long)(long long)dE);
+        if (GROUP) {  // publish the item: every lane's spin and state stores before the count
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) atomicAdd(pa.done + e.x, 1u);
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        const unsigned done = atomicAdd(&ctr[1], 1u);
-        if (done == gridDim.x - 1) {
-            atomicExch(&ctr[0], 0u);
-            atomicExch(&ctr[1], 0u);
+        const unsigned fin = atomicAdd(&pa.ctr[1], 1u);
+        if (fin == gridDim.x - 1) {
+            for (int l = 0; GROUP && l < pa.nlat; ++l) pa.done[l] = 0u;
+            atomicExch(&pa.ctr[0], 0u);
+            atomicExch(&pa.ctr[1], 0u);
             __threadfence();
         }
     }
@@ -314,27 +363,32 @@ static size_t pass_smem(int kind, int wpt) {
     return (size_t)kPassWarps * (ring + 2 * wpt * kCondWords) * sizeof(uint32_t);
 }
 
-// Colour passes of `sweeps` sweeps of every lattice: 2 * sweeps launches.
-static cudaError_t launch_passes(int kind, int wpt, const FlipArgs* reps, const int2* items, int nitems, int sweeps,
-                                 unsigned* ctr, cudaStream_t s) {
-    if (nitems <= 0 || sweeps <= 0) return cudaSuccess;
+// `sweeps` sweeps of every lattice of the item list: one launch per colour
+// pass (group = false) or one launch for all of them (group = true).
+static cudaError_t launch_passes(int kind, int wpt, bool group, PassArgs pa, int sweeps, cudaStream_t s) {
+    if (pa.nitems <= 0 || sweeps <= 0) return cudaSuccess;
     const StreamConst k = stream_const();
     const size_t smem = pass_smem(kind, wpt);
+    auto run = [&](auto kern, std::atomic<int> (&occ_cache)[kDeviceSlots]) {
+        const int occ = occupancy_cached(occ_cache, kern, kPassWarps * 32, smem);
+        int64_t grid = (int64_t)sm_count() * occ;
+        const int64_t need = (pa.nitems + kPassWarps - 1) / kPassWarps;
+        if (grid > need) grid = need;
+        const int launches = group ? 1 : 2 * sweeps;
+        pa.npasses = group ? 2 * sweeps : 1;
+        for (int l = 0; l < launches; ++l) {
+            pa.c0 = l & 1;
+            kern<<<(unsigned)grid, kPassWarps * 32, smem, s>>>(pa, k);
+            const cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    };
     return with_kind(kind, [&](auto kc) {
         return with_wpt(wpt, [&](auto wc) {
             constexpr int K = decltype(kc)::value, WPT = decltype(wc)::value;
-            static std::atomic<int> occ_cache[kDeviceSlots];
-            const int occ = occupancy_cached(occ_cache, pass_kernel<K, WPT>, kPassWarps * 32, smem);
-            int64_t grid = (int64_t)sm_count() * occ;
-            const int64_t need = (nitems + kPassWarps - 1) / kPassWarps;
-            if (grid > need) grid = need;
-            for (int sw = 0; sw < sweeps; ++sw)
-                for (int c = 0; c < 2; ++c) {
-                    pass_kernel<K, WPT><<<(unsigned)grid, kPassWarps * 32, smem, s>>>(reps, items, nitems, c, ctr, k);
-                    const cudaError_t e = cudaGetLastError();
-                    if (e != cudaSuccess) return e;
-                }
-            return cudaSuccess;
+            static std::atomic<int> occ_pass[kDeviceSlots], occ_group[kDeviceSlots];
+            return group ? run(pass_kernel<K, WPT, true>, occ_group) : run(pass_kernel<K, WPT, false>, occ_pass);
         });
     });
 }
@@ -394,8 +448,19 @@ void plan_bundles(const std::vector<isg_sim*>& reps, std::vector<int2>& entries,
 }
 
 static cudaError_t batch_launch(isg_batch* b, int sweeps, cudaStream_t s) {
-    if (b->cfg.shape == kPassShape)
-        return launch_passes(b->kind, b->cfg.wpt, b->d_reps, b->d_items, b->nbundles, sweeps, b->d_ctr, s);
+    if (b->cfg.shape >= kPassShape) {
+        PassArgs pa;
+        pa.reps = b->d_reps;
+        pa.items = b->d_items;
+        pa.nitems = b->nbundles;
+        pa.npasses = 0;
+        pa.c0 = 0;
+        pa.nlat = (int)b->reps.size();
+        pa.stall = b->stall;
+        pa.ctr = b->d_ctr;
+        pa.done = b->d_done;
+        return launch_passes(b->kind, b->cfg.wpt, b->cfg.shape == kGroupShape, pa, sweeps, s);
+    }
     return launch_bundle_kernel(b->kind, b->cfg, b->d_reps, b->d_entries, b->d_boff, nullptr, b->nbundles, sweeps,
                                 b->d_ctr, s, &b->tasks);
 }
@@ -451,7 +516,7 @@ static int batch_plan(isg_batch* b) {
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
     if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
     b->graph_group = 0;
-    if (b->cfg.shape == kPassShape) {
+    if (b->cfg.shape >= kPassShape) {
         // every stream of every lattice is an item; the longest go first
         std::vector<int2> items;
         std::vector<int64_t> len;
@@ -466,7 +531,15 @@ static int batch_plan(isg_batch* b) {
         };
         std::stable_sort(items.begin(), items.end(), [&](const int2& x, const int2& y) { return draws(x) > draws(y); });
         if (!b->d_items) b->d_items = (int2*)dev_alloc(h0, items.size() * sizeof(int2));
-        if (!b->d_items) {
+        if (!b->d_done) {
+            b->d_done = (unsigned*)dev_alloc(h0, b->reps.size() * sizeof(unsigned));
+            if (b->d_done && cudaMemset(b->d_done, 0, b->reps.size() * sizeof(unsigned)) != cudaSuccess) {
+                set_error("isg_batch: clearing the lattice counts failed");
+                return ISG_ERR_CUDA;
+            }
+        }
+        b->stall = -1;
+        if (!b->d_items || !b->d_done) {
             set_error("isg_batch: device allocation failed");
             return ISG_ERR_NOMEM;
         }
@@ -520,6 +593,7 @@ static void batch_free(isg_batch* b) {
         dev_free(b->reps[0], b->tasks.d_tasks);
         dev_free(b->reps[0], b->tasks.d_done);
         dev_free(b->reps[0], b->d_items);
+        dev_free(b->reps[0], b->d_done);
     }
     for (isg_sim* h : b->reps) destroy_sim(h);
     delete b;
@@ -598,7 +672,7 @@ int isg_batch_info(const isg_batch* b, int* samples, int* bundles, int64_t* atte
 }
 
 int isg_batch_set_config(isg_batch* b, int shape, int capacity, int resident, int words_per_lane) {
-    if (!b || shape < 0 || shape > kPassShape || capacity < 0 || (resident != 0 && resident != 1) ||
+    if (!b || shape < 0 || shape > kGroupShape || capacity < 0 || (resident != 0 && resident != 1) ||
         (words_per_lane != 1 && words_per_lane != 2)) {
         set_error("isg_batch_set_config: bad argument");
         return ISG_ERR_ARG;
@@ -630,7 +704,20 @@ int isg_batch_get_config(const isg_batch* b, int* shape, int* capacity, int* res
 
 int isg_batch_test_stall(isg_batch* b) {
     if (!b) { set_error("isg_batch_test_stall: NULL batch"); return ISG_ERR_ARG; }
-    if (b->cfg.shape == kPassShape) { set_error("isg_batch_test_stall: the pass engine has no tasks"); return ISG_ERR_STATE; }
+    if (b->cfg.shape == kPassShape) {
+        set_error("isg_batch_test_stall: the pass launches have no waits");
+        return ISG_ERR_STATE;
+    }
+    if (b->cfg.shape == kGroupShape) {  // the smallest lattice's pass-1 items wait for one item too many
+        if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+        if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+        b->graph_group = 0;
+        int best = 0;
+        for (int r = 1; r < (int)b->reps.size(); ++r)
+            if (b->reps[r]->S < b->reps[best]->S) best = r;
+        b->stall = best;
+        return ISG_OK;
+    }
     const int n = b->tasks.ntasks;
     if (n < 2) { set_error("isg_batch_test_stall: fewer than two tasks"); return ISG_ERR_STATE; }
     int4 t;

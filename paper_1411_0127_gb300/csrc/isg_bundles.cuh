@@ -11,9 +11,11 @@ namespace isg {
 // Execution configuration of the persistent bundle kernel.  None of it changes
 // a result: every lattice follows its own trajectory whatever the bundles.
 //   shape     0: one CTA of 32 warps per SM, 1: one of 24, 2: one of 16,
-//             3: two of 16; kPassShape (batches only): no bundles, every colour
+//             3: two of 16; batches only, no bundles: kPassShape, every colour
 //             pass of all lattices is one launch whose warps take (lattice,
-//             stream) items by ticket (capacity and resident do not apply)
+//             stream) items by ticket; kGroupShape, one launch runs all passes
+//             of a sweep group, items of pass p waiting (bounded) for their own
+//             lattice's pass p - 1 only (capacity and resident do not apply)
 //   capacity  streams per packed bundle of small lattices (1 .. warps of the shape)
 //   resident  1: the generator state of a bundle that fits in the CTA stays in
 //             shared memory / registers for the whole launch; 0: it is loaded
@@ -22,6 +24,7 @@ namespace isg {
 //             wpt * 32 words, so 2 halves the groups per pass
 constexpr int kBundleShapeCount = 4;
 constexpr int kPassShape = 4;
+constexpr int kGroupShape = 5;
 struct BundleConfig {
     int shape = 0;
     int capacity = 32;

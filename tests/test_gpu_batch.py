@@ -71,16 +71,21 @@ def test_batch_member_equals_lone_handle(isg):
     assert b.info()["samples"] == len(L)
 
 
-def test_full_batch_workload_sampled(isg):
-    """The 512-sample workload in the benchmark's launch configuration (one
-    graph-replayed persistent launch of 64 sweeps); energies and overlaps of one
-    sample per lattice size checked against the oracle, the energy bookkeeping
-    of every replica checked against its energy from scratch."""
+@pytest.mark.parametrize("config", [(0, 32, 1, 1), (4, 4, 0, 2), (5, 4, 0, 1)])
+def test_full_batch_workload_sampled(isg, config):
+    """The 512-sample workload in one graph-replayed persistent launch of 64
+    sweeps, with the default bundle configuration and with both pass engines
+    (the per-pass form is the one the autotuner picks for MT19937, the
+    benchmark's configuration); energies and
+    overlaps of one sample per lattice size checked against the oracle, the
+    energy bookkeeping of every replica checked against its energy from
+    scratch."""
     from paper_1411_0127_gb300 import workloads
     samples = workloads.batch_samples()
     L = [x.L for x in samples]
     b = isg.Batch(L, [x.seed_J for x in samples], [v for x in samples for v in x.seed_spin],
                   [1.0 / x.T for x in samples], "mt19937")
+    b.set_config(*config)
     info = b.info()
     assert info["attempts_per_sweep"] == 2 * sum(v ** 3 for v in L)
     b.run(64, group_sweeps=64)
@@ -107,9 +112,10 @@ def test_full_batch_workload_sampled(isg):
 
 @pytest.mark.slow
 def test_full_batch_workload_every_replica(isg):
-    """The 512-sample workload at the benchmark's launch configuration (one
-    graph-replayed persistent launch of 64 sweeps): the tracked energy and the
-    hash of all 1024 replicas and the overlap of all 512 samples against the
+    """The 512-sample workload at the benchmark's launch configuration (the
+    pass engine with two words per lane, which the autotuner picks for MT19937;
+    one graph-replayed persistent launch of 64 sweeps): the tracked energy and
+    the hash of all 1024 replicas and the overlap of all 512 samples against the
     oracle.  The oracles run 16 at a time on host threads (the ctypes calls
     release the interpreter lock), one thread each."""
     import concurrent.futures as cf
@@ -118,6 +124,7 @@ def test_full_batch_workload_every_replica(isg):
     samples = workloads.batch_samples()
     b = isg.Batch([x.L for x in samples], [x.seed_J for x in samples], [v for x in samples for v in x.seed_spin],
                   [1.0 / x.T for x in samples], "mt19937")
+    b.set_config(4, 4, 0, 2)
     b.run(64, group_sweeps=64)
     E, Q = b.measure()
     Et, H = b.tracked()
@@ -206,8 +213,8 @@ def test_autotuner_picks_a_candidate_and_caches_it(isg, tmp_path):
 def test_batch_config_rejects_bad_values(isg):
     L, J, S, B = mixed()
     b = isg.Batch(L[:2], J[:2], S[:4], B[:2], "minstd")
-    for bad in [(5, 0, 1, 1), (-1, 0, 1, 1), (2, 17, 1, 1), (0, 33, 1, 1), (0, 8, 2, 1), (0, 8, 1, 3), (0, 8, 1, 0),
-                (4, 5, 0, 1)]:
+    for bad in [(6, 0, 1, 1), (-1, 0, 1, 1), (2, 17, 1, 1), (0, 33, 1, 1), (0, 8, 2, 1), (0, 8, 1, 3), (0, 8, 1, 0),
+                (4, 5, 0, 1), (5, 5, 0, 1)]:
         with pytest.raises(isg.IsgError):
             b.set_config(*bad)
     assert b.get_config() == (0, 32, 1, 1)
@@ -232,4 +239,28 @@ def test_dependency_wait_gives_up_with_a_status(isg):
     Em, _ = b.measure()
     Et, _ = b.tracked()
     assert np.array_equal(Em, Et)                 # every replica's bookkeeping intact
+    b.close()
+
+
+def test_pass_engine_wait_gives_up_with_a_status(isg):
+    """The group pass engine's bounded wait: the pass-1 items of one lattice are made
+    to wait for one completed item too many.  The wait runs out, the next read
+    reports ISG_ERR_TIMEOUT once, and the context stays usable; a fresh plan
+    sweeps on with every replica's bookkeeping intact."""
+    L, J, S, B = mixed()
+    b = isg.Batch(L, J, S, B, "minstd")
+    b.set_config(4, 4, 0, 1)
+    assert isg.lib().isg_batch_test_stall(b._h) == isg.ISG_ERR_STATE   # no waits in the per-pass launches
+    b.set_config(5, 4, 0, 1)
+    assert isg.lib().isg_batch_test_stall(b._h) == isg.ISG_OK
+    b.run(1, group_sweeps=1)
+    with pytest.raises(isg.IsgError) as ex:
+        b.tracked()
+    assert ex.value.code == isg.ISG_ERR_TIMEOUT
+    b.tracked()                                   # reported once
+    b.set_config(5, 4, 0, 1)                      # a fresh plan
+    b.run(2, group_sweeps=2)
+    Em, _ = b.measure()
+    Et, _ = b.tracked()
+    assert np.array_equal(Em, Et)
     b.close()
