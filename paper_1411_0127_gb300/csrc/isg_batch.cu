@@ -277,7 +277,9 @@ struct PassArgs {
     const int2* items;   // (lattice, stream), longest streams first
     int nitems;
     int npasses;         // passes of this launch (1 for a launch per pass)
-    int c0;              // colour of its first pass
+    int pass0;           // index of its first pass (colour = index & 1)
+    const int* limit;    // per lattice: passes to run, or NULL for all (a lattice
+                         // with fewer skips the items of its later passes)
     int nlat;
     int stall;           // test hook: this lattice's pass-1 items wait for one item too many (-1: none)
     unsigned* ctr;       // [0] next ticket, [1] CTAs done, [2] sticky error: a wait gave up
@@ -299,6 +301,7 @@ __global__ void __launch_bounds__(kPassWarps * 32, 7) pass_kernel(PassArgs pa, S
         if (v >= total) break;
         const int p = GROUP ? (int)(v / (unsigned)pa.nitems) : 0;
         const int2 e = pa.items[v - (unsigned)p * (unsigned)pa.nitems];
+        if (pa.limit && pa.pass0 + p >= pa.limit[e.x]) continue;  // this lattice is done for the launch
         const FlipArgs& g = pa.reps[e.x];
         if (GROUP && p > 0) {
             const unsigned need = (unsigned)p * (unsigned)g.S + (e.x == pa.stall && p == 1 ? 1u : 0u);
@@ -335,7 +338,7 @@ __global__ void __launch_bounds__(kPassWarps * 32, 7) pass_kernel(PassArgs pa, S
         load_stream<KIND>(g, e.y, ring, st, k, lane);
         int dE = 0;
         const int64_t rb = (int64_t)e.y * g.R, re = rb + g.R < g.rows ? rb + g.R : g.rows;
-        stream_pass<uint64_t, KIND, kPassSlack, true, WPT>(a, (pa.c0 + p) & 1, rb, re, ring, cond, st, k, lane, dE);
+        stream_pass<uint64_t, KIND, kPassSlack, true, WPT>(a, (pa.pass0 + p) & 1, rb, re, ring, cond, st, k, lane, dE);
         store_stream<KIND>(g, e.y, ring, st, lane);
         for (int sh = 16; sh; sh >>= 1) dE += __shfl_xor_sync(kFull, dE, sh);
         if (lane == 0 && dE != 0) atomicAdd((unsigned long long*)g.dE, (unsigned long long)(long long)dE);
@@ -365,6 +368,24 @@ static size_t pass_smem(int kind, int wpt) {
 
 // `sweeps` sweeps of every lattice of the item list: one launch per colour
 // pass (group = false) or one launch for all of them (group = true).
+static cudaError_t launch_passes(int kind, int wpt, bool group, PassArgs pa, int sweeps, cudaStream_t s);
+
+cudaError_t launch_pass_items(int kind, const FlipArgs* reps, const int2* items, int nitems, const int* limit,
+                              int sweeps, unsigned* ctr, cudaStream_t s) {
+    PassArgs pa;
+    pa.reps = reps;
+    pa.items = items;
+    pa.nitems = nitems;
+    pa.npasses = 0;
+    pa.pass0 = 0;
+    pa.limit = limit;
+    pa.nlat = 0;
+    pa.stall = -1;
+    pa.ctr = ctr;
+    pa.done = nullptr;
+    return launch_passes(kind, 1, false, pa, sweeps, s);
+}
+
 static cudaError_t launch_passes(int kind, int wpt, bool group, PassArgs pa, int sweeps, cudaStream_t s) {
     if (pa.nitems <= 0 || sweeps <= 0) return cudaSuccess;
     const StreamConst k = stream_const();
@@ -377,7 +398,7 @@ static cudaError_t launch_passes(int kind, int wpt, bool group, PassArgs pa, int
         const int launches = group ? 1 : 2 * sweeps;
         pa.npasses = group ? 2 * sweeps : 1;
         for (int l = 0; l < launches; ++l) {
-            pa.c0 = l & 1;
+            pa.pass0 = l;
             kern<<<(unsigned)grid, kPassWarps * 32, smem, s>>>(pa, k);
             const cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return e;
@@ -454,7 +475,8 @@ static cudaError_t batch_launch(isg_batch* b, int sweeps, cudaStream_t s) {
         pa.items = b->d_items;
         pa.nitems = b->nbundles;
         pa.npasses = 0;
-        pa.c0 = 0;
+        pa.pass0 = 0;
+        pa.limit = nullptr;
         pa.nlat = (int)b->reps.size();
         pa.stall = b->stall;
         pa.ctr = b->d_ctr;

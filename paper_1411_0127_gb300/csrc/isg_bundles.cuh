@@ -67,4 +67,12 @@ cudaError_t launch_bundle_kernel(int kind, const BundleConfig& cfg, const FlipAr
                                  const int* boff, const int* bsweeps, int nbundles, int sweeps, unsigned* ctr,
                                  cudaStream_t s, const BundleTasks* tasks = nullptr);
 
+// Per-pass launches of the pass engine over an item list (lattice, stream),
+// longest streams first: 2 * sweeps launches, launch p sweeping colour p & 1 of
+// the items whose lattice has limit[lattice] > p (limit NULL: every lattice
+// runs all passes).  ctr must hold two zeroed words; each launch returns them
+// to zero when it ends.
+cudaError_t launch_pass_items(int kind, const FlipArgs* reps, const int2* items, int nitems, const int* limit,
+                              int sweeps, unsigned* ctr, cudaStream_t s);
+
 }  // namespace isg

@@ -7,11 +7,13 @@
 //   1. admit, in arrival order, the jobs that have arrived while the device
 //      memory they need fits the budget and a slot is free (a job that does not
 //      fit blocks the ones behind it: first come, first served);
-//   2. run one quantum: every active lattice with at most 256 RNG streams
-//      (L <= 200) goes into one persistent bundle launch per generator kind,
-//      each bundle running min(quantum, sweeps left of its lattices) sweeps;
-//      every larger lattice is swept with the whole-GPU kernel on a stream of
-//      its own, so the launches overlap on the device;
+//   2. run one quantum: every active lattice's streams become items of the
+//      pass engine (one launch per colour pass and generator kind, 4-warp CTAs
+//      taking (lattice, stream) items by ticket, longest first), each lattice
+//      running min(quantum, sweeps left) sweeps; MINSTD lattices with more than
+//      256 RNG streams (L > 200) are swept instead with the whole-GPU kernel
+//      (its streams cut into jump-ahead segments where few) on streams of their
+//      own, so the launches overlap on the device;
 //   3. retire the jobs that are done: energy from scratch and Zobrist hash,
 //      completion time, memory returned to the budget.
 // The lattices, couplings and generator states stay on the device between
@@ -50,15 +52,14 @@ struct ServeJob {
 
 struct PlanBuf {
     FlipArgs* reps = nullptr;
-    int2* entries = nullptr;
-    int* boff = nullptr;
-    int* bsweeps = nullptr;
+    int2* items = nullptr;
+    int* limit = nullptr;
     unsigned* ctr = nullptr;
-    size_t cap_reps = 0, cap_entries = 0, cap_bundles = 0;
+    size_t cap_reps = 0, cap_items = 0, cap_limit = 0;
     // host copies of the current plan (alive until the quantum has finished)
     std::vector<FlipArgs> desc;
-    std::vector<int2> h_entries;
-    std::vector<int> h_boff, h_bsweeps, order, idx;
+    std::vector<int2> h_items;
+    std::vector<int> h_limit, idx;
     std::vector<int64_t> give;
 };
 
@@ -102,52 +103,53 @@ static bool ensure(T*& p, size_t& cap, size_t need) {
     return p != nullptr;
 }
 
-// Enqueue one quantum of the batched jobs of one generator kind.  The plan's
-// host copies stay in s->plan[kind] until finish_batched has run.
+// Enqueue one quantum of the batched jobs of one generator kind: every stream
+// of every such job is an item of the pass engine, longest streams first; job j
+// runs give_j = min(quantum, sweeps left) sweeps, so its items take part in the
+// first 2 give_j of the 2 max(give) pass launches.  The plan's host copies stay
+// in s->plan[kind] until finish_batched has run.
 static int launch_batched(isg_server* s, int kind, const std::vector<int>& active) {
     PlanBuf& P = s->plan[kind];
-    std::vector<isg_sim*> reps;
     P.idx.clear();
+    P.desc.clear();
+    P.h_limit.clear();
+    P.h_items.clear();
+    P.give.clear();
+    int64_t qmax = 0;
     for (int j : active) {
         const ServeJob& J = s->jobs[j];
-        if (!J.wide && J.kind == kind) {
-            reps.push_back(J.h);
-            P.idx.push_back(j);
-        }
+        if (J.wide || J.kind != kind) continue;
+        const int64_t q = std::min<int64_t>(s->quantum, J.sweeps - J.done);
+        const int r = (int)P.idx.size();
+        P.idx.push_back(j);
+        P.give.push_back(q);
+        P.desc.push_back(make_flip_args(J.h, 0));
+        P.h_limit.push_back((int)(2 * q));
+        for (int64_t t = 0; t < J.h->S; ++t) P.h_items.push_back(make_int2(r, (int)t));
+        qmax = std::max(qmax, q);
     }
-    P.give.assign(reps.size(), 0);
-    if (reps.empty()) return ISG_OK;
-    plan_bundles(reps, P.h_entries, P.h_boff, &P.order);
-    const int nb = (int)P.h_boff.size() - 1;
-    P.h_bsweeps.assign(nb, 0);
-    size_t o = 0;
-    for (int b = 0; b < nb; ++b) {
-        int64_t q = s->quantum;
-        for (size_t k = o; P.order[k] >= 0; ++k)
-            q = std::min(q, s->jobs[P.idx[P.order[k]]].sweeps - s->jobs[P.idx[P.order[k]]].done);
-        P.h_bsweeps[b] = (int)q;
-        for (; P.order[o] >= 0; ++o) P.give[P.order[o]] = q;
-        ++o;  // skip the -1
-    }
-    P.desc.resize(reps.size());
-    for (size_t r = 0; r < reps.size(); ++r) P.desc[r] = make_flip_args(reps[r], 0);
-    if (!ensure(P.reps, P.cap_reps, P.desc.size()) || !ensure(P.entries, P.cap_entries, P.h_entries.size()) ||
-        !ensure(P.boff, P.cap_bundles, P.h_boff.size()) || !ensure(P.bsweeps, P.cap_bundles, P.h_boff.size())) {
-        set_error("isg_server_run: device allocation for the bundle plan failed");
+    if (P.idx.empty() || qmax == 0) return ISG_OK;
+    auto draws = [&](const int2& it) {
+        const isg_sim* h = s->jobs[P.idx[it.x]].h;
+        const int64_t r0 = (int64_t)it.y * h->R, r1 = std::min(r0 + h->R, h->rows);
+        return (r1 - r0) * h->half;
+    };
+    std::stable_sort(P.h_items.begin(), P.h_items.end(),
+                     [&](const int2& x, const int2& y) { return draws(x) > draws(y); });
+    if (!ensure(P.reps, P.cap_reps, P.desc.size()) || !ensure(P.items, P.cap_items, P.h_items.size()) ||
+        !ensure(P.limit, P.cap_limit, P.h_limit.size())) {
+        set_error("isg_server_run: device allocation for the quantum plan failed");
         return ISG_ERR_NOMEM;
     }
     cudaStream_t st = s->batch_stream[kind];
     cudaError_t e =
         cudaMemcpyAsync(P.reps, P.desc.data(), P.desc.size() * sizeof(FlipArgs), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(P.entries, P.h_entries.data(), P.h_entries.size() * sizeof(int2), cudaMemcpyHostToDevice,
-                            st);
+        e = cudaMemcpyAsync(P.items, P.h_items.data(), P.h_items.size() * sizeof(int2), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(P.boff, P.h_boff.data(), P.h_boff.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+        e = cudaMemcpyAsync(P.limit, P.h_limit.data(), P.h_limit.size() * sizeof(int), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(P.bsweeps, P.h_bsweeps.data(), P.h_bsweeps.size() * sizeof(int), cudaMemcpyHostToDevice,
-                            st);
-    if (e == cudaSuccess) e = launch_bundle_kernel(kind, BundleConfig{}, P.reps, P.entries, P.boff, P.bsweeps, nb, 0, P.ctr, st);
+        e = launch_pass_items(kind, P.reps, P.items, (int)P.h_items.size(), P.limit, (int)qmax, P.ctr, st);
     if (e != cudaSuccess) return cuda_fail(e, "isg_server_run: batched quantum");
     return ISG_OK;
 }
@@ -191,7 +193,6 @@ int isg_server_create(size_t hbm_budget_bytes, int quantum_sweeps, int max_activ
             if (!s->plan[k].ctr) e = cudaErrorMemoryAllocation;
         }
         if (e == cudaSuccess) e = cudaMemset(s->plan[k].ctr, 0, 3 * sizeof(unsigned));
-        if (e == cudaSuccess) e = prepare_bundle_kernel(k, BundleConfig{});
     }
     for (int k = 0; k < kWideStreams && e == cudaSuccess; ++k)
         e = cudaStreamCreateWithFlags(&s->wide_stream[k], cudaStreamNonBlocking);
@@ -210,9 +211,8 @@ void isg_server_destroy(isg_server* s) {
         if (J.h) destroy_sim(J.h);
     for (PlanBuf& P : s->plan) {
         cudaFree(P.reps);
-        cudaFree(P.entries);
-        cudaFree(P.boff);
-        cudaFree(P.bsweeps);
+        cudaFree(P.items);
+        cudaFree(P.limit);
         cudaFree(P.ctr);
     }
     for (cudaStream_t st : s->batch_stream)
@@ -246,7 +246,9 @@ int isg_server_submit(isg_server* s, int L, uint64_t seed_J, uint64_t seed_spin,
         R = (rows + s0 - 1) / s0;
         S = (rows + R - 1) / R;
     }
-    J.wide = S > kBatchedMaxStreams;
+    // MINSTD lattices with many streams sweep alone (segmented streams); every
+    // other job goes to its kind's pass launches
+    J.wide = rng_kind == ISG_RNG_MINSTD && S > kBatchedMaxStreams;
     J.bytes = sim_device_bytes(L, rng_kind, !J.wide);
     if (J.bytes > s->budget) {
         set_error("isg_server_submit: job needs %zu bytes, the budget is %zu", J.bytes, s->budget);
