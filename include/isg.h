@@ -272,9 +272,8 @@ int isg_batch_tracked(isg_batch *b, int64_t *E, uint64_t *H, void *cuda_stream);
  * hbm_budget_bytes and fewer than max_active jobs (<= 0: 4096) are on the
  * device; every quantum of quantum_sweeps sweeps (<= 0: 64) sweeps all active
  * jobs at once (the streams of all active jobs of one generator kind as items
- * of one launch per colour pass, longest first; MINSTD lattices with more than
- * 256 RNG streams each on a CUDA stream of its own, overlapping); finished
- * jobs release their memory at once.  The paper has no serving layer; each job
+ * of one launch per colour pass, longest first; lattices are held in 64-bit
+ * words); finished jobs release their memory at once.  The paper has no serving layer; each job
  * follows exactly the trajectory of a lone isg_create handle. */
 typedef struct isg_server isg_server;
 int isg_server_create(size_t hbm_budget_bytes, int quantum_sweeps, int max_active, isg_server **out);

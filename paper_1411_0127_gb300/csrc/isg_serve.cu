@@ -10,10 +10,8 @@
 //   2. run one quantum: every active lattice's streams become items of the
 //      pass engine (one launch per colour pass and generator kind, 4-warp CTAs
 //      taking (lattice, stream) items by ticket, longest first), each lattice
-//      running min(quantum, sweeps left) sweeps; MINSTD lattices with more than
-//      256 RNG streams (L > 200) are swept instead with the whole-GPU kernel
-//      (its streams cut into jump-ahead segments where few) on streams of their
-//      own, so the launches overlap on the device;
+//      running min(quantum, sweeps left) sweeps; the three kinds' launches run
+//      on streams of their own;
 //   3. retire the jobs that are done: energy from scratch and Zobrist hash,
 //      completion time, memory returned to the budget.
 // The lattices, couplings and generator states stay on the device between
@@ -32,9 +30,7 @@
 
 namespace isg {
 
-constexpr int kWideStreams = 8;
 constexpr int kKinds = 3;   // generator kinds: one bundle plan and stream each
-constexpr int64_t kBatchedMaxStreams = 256;
 
 struct ServeJob {
     int L = 0, kind = 0;
@@ -43,7 +39,6 @@ struct ServeJob {
     int64_t sweeps = 0, done = 0;
     isg_sim* h = nullptr;
     size_t bytes = 0;
-    bool wide = false;
     int status = 0;  // 0 waiting, 1 active, 2 finished, < 0 failed (ISG_ERR_*)
     double t_admit = -1.0, t_done = -1.0;
     int64_t E = 0;
@@ -73,7 +68,6 @@ struct isg_server {
     std::vector<isg::ServeJob> jobs;
     isg::PlanBuf plan[isg::kKinds];
     cudaStream_t batch_stream[isg::kKinds] = {nullptr, nullptr, nullptr};
-    cudaStream_t wide_stream[isg::kWideStreams] = {};
     // statistics of the last run
     int64_t iterations = 0, attempts = 0;
     double wall = 0.0, busy = 0.0;
@@ -118,7 +112,7 @@ static int launch_batched(isg_server* s, int kind, const std::vector<int>& activ
     int64_t qmax = 0;
     for (int j : active) {
         const ServeJob& J = s->jobs[j];
-        if (J.wide || J.kind != kind) continue;
+        if (J.kind != kind) continue;
         const int64_t q = std::min<int64_t>(s->quantum, J.sweeps - J.done);
         const int r = (int)P.idx.size();
         P.idx.push_back(j);
@@ -194,8 +188,6 @@ int isg_server_create(size_t hbm_budget_bytes, int quantum_sweeps, int max_activ
         }
         if (e == cudaSuccess) e = cudaMemset(s->plan[k].ctr, 0, 3 * sizeof(unsigned));
     }
-    for (int k = 0; k < kWideStreams && e == cudaSuccess; ++k)
-        e = cudaStreamCreateWithFlags(&s->wide_stream[k], cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         isg_server_destroy(s);
         return cuda_fail(e, "isg_server_create");
@@ -217,8 +209,6 @@ void isg_server_destroy(isg_server* s) {
     }
     for (cudaStream_t st : s->batch_stream)
         if (st) cudaStreamDestroy(st);
-    for (cudaStream_t st : s->wide_stream)
-        if (st) cudaStreamDestroy(st);
     delete s;
 }
 
@@ -238,18 +228,7 @@ int isg_server_submit(isg_server* s, int L, uint64_t seed_J, uint64_t seed_spin,
     J.beta = beta;
     J.sweeps = sweeps;
     J.arrival = arrival_s;
-    int64_t R = 0, S = 0;
-    {
-        const int64_t rows = (int64_t)L * L;
-        int64_t s0 = (int64_t)L * L * L / 32768;
-        s0 = s0 < 1 ? 1 : (s0 > 8192 ? 8192 : s0);
-        R = (rows + s0 - 1) / s0;
-        S = (rows + R - 1) / R;
-    }
-    // MINSTD lattices with many streams sweep alone (segmented streams); every
-    // other job goes to its kind's pass launches
-    J.wide = rng_kind == ISG_RNG_MINSTD && S > kBatchedMaxStreams;
-    J.bytes = sim_device_bytes(L, rng_kind, !J.wide);
+    J.bytes = sim_device_bytes(L, rng_kind, true);
     if (J.bytes > s->budget) {
         set_error("isg_server_submit: job needs %zu bytes, the budget is %zu", J.bytes, s->budget);
         return ISG_ERR_ARG;
@@ -290,7 +269,7 @@ int isg_server_run(isg_server* s, double time_limit_s) {
         while (next < order.size()) {
             ServeJob& J = s->jobs[order[next]];
             if (J.arrival > now || used + J.bytes > s->budget || (int)active.size() >= s->max_active) break;
-            const int rc = create_sim(J.L, J.seed_J, J.seed_spin, J.seed_spin, J.beta, J.kind, !J.wide, &J.h);
+            const int rc = create_sim(J.L, J.seed_J, J.seed_spin, J.seed_spin, J.beta, J.kind, true, &J.h);
             ++next;
             if (rc) {
                 J.status = rc;
@@ -312,18 +291,8 @@ int isg_server_run(isg_server* s, double time_limit_s) {
             }
             continue;
         }
-        // 2. one quantum: wide lattices on their own streams, the rest in bundles
+        // 2. one quantum: per generator kind, pass launches over all its jobs' streams
         const double tq = now_s(t0);
-        int w = 0;
-        for (int j : active) {
-            ServeJob& J = s->jobs[j];
-            if (!J.wide) continue;
-            const int64_t q = std::min<int64_t>(s->quantum, J.sweeps - J.done);
-            const int rc = isg_sweep(J.h, q, s->wide_stream[w++ % kWideStreams]);
-            if (rc) return rc;
-            J.done += q;
-            s->attempts += q * (int64_t)J.L * J.L * J.L;
-        }
         for (int k = 0; k < kKinds; ++k) {
             const int rc = launch_batched(s, k, active);
             if (rc) return rc;
@@ -331,10 +300,6 @@ int isg_server_run(isg_server* s, double time_limit_s) {
         for (int k = 0; k < kKinds; ++k) {
             const int rc = finish_batched(s, k);
             if (rc) return rc;
-        }
-        for (cudaStream_t st : s->wide_stream) {
-            const cudaError_t e = cudaStreamSynchronize(st);
-            if (e != cudaSuccess) return cuda_fail(e, "isg_server_run: quantum");
         }
         s->busy += now_s(t0) - tq;
         ++s->iterations;
