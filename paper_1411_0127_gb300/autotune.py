@@ -1,7 +1,7 @@
-"""Autotuner of the batched persistent engine.
+"""Autotuner of the batched engine.
 
 The batch's execution configuration (isg_batch_set_config: CTA shape of the
-persistent bundle kernel or the per-pass engine, streams per bundle,
+persistent bundle kernel or one of the two pass engines, streams per bundle,
 generator-state placement, words per lane) changes its speed but never its
 results, so the tuner can pick it by measurement alone.  It times every
 candidate on a twin of the batch (same samples, seeds and temperatures, a

@@ -1,5 +1,7 @@
-// isg_bundles.cuh -- bundle planning and the persistent bundle kernel, shared by
-// the batched engine (isg_batch.cu) and the request server (isg_serve.cu).
+// isg_bundles.cuh -- the multi-lattice engines of the batched engine
+// (isg_batch.cu): bundle planning and the persistent bundle kernel, and the
+// per-pass launches over (lattice, stream) items that the request server
+// (isg_serve.cu) also uses.
 #pragma once
 
 #include <vector>
