@@ -229,48 +229,55 @@ __device__ __forceinline__ uint64_t compact32(uint64_t v) {
     return v;
 }
 
-// 32 bits h = 32m .. 32m + 31 of colour c's row r.
-template <typename Word>
-__device__ __forceinline__ uint32_t row_bits32(const IoGeom& g, int c, int64_t r, int m) {
-    constexpr int w = 8 * sizeof(Word);
-    const Word* P = (const Word*)(g.planes + (size_t)(4 * c) * g.plane_bytes) + r * g.W;
-    return (uint32_t)(P[(32 * m) / w] >> ((32 * m) % w));
-}
-
-// planes -> packed bits, L % 64 == 0: one thread per 64 sites of a row.
+// planes -> packed bits, L % 64 == 0: one thread per plane word slot (row r,
+// word k) of both colours, i.e. w / 32 runs of 64 sites of the row; a last word
+// with fewer valid sites (64-bit words when L / 2 is an odd multiple of 32)
+// writes only its valid runs.  Indices fit in 32 bits (rows * W < 2^27).
 template <typename Word>
 __global__ void unpack_spins_bits64_kernel(IoGeom g, uint64_t* out) {
-    const int per_row = g.L / 64;
-    const int64_t n = g.rows * per_row;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = t / per_row;
-        const int m = (int)(t - r * per_row);
-        const int pr = (int)((r % g.L + r / g.L) & 1);
-        const uint64_t red = spread32(row_bits32<Word>(g, 0, r, m));
-        const uint64_t blue = spread32(row_bits32<Word>(g, 1, r, m));
-        out[t] = (red << pr) | (blue << (1 - pr));
+    constexpr int w = 8 * sizeof(Word);
+    const unsigned W = (unsigned)g.W, L = (unsigned)g.L, half = (unsigned)g.half;
+    const unsigned n = (unsigned)g.rows * W;
+    const Word* P0 = (const Word*)g.planes;
+    const Word* P1 = (const Word*)(g.planes + (size_t)4 * g.plane_bytes);
+    const unsigned stride = gridDim.x * blockDim.x;
+    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
+        const unsigned r = t / W, k = t - r * W;
+        const unsigned pr = (r % L + r / L) & 1u;
+        const Word red = P0[t], blue = P1[t];
+        uint64_t* o = out + (size_t)r * (L / 64) + (size_t)k * (w / 32);
+#pragma unroll
+        for (int q = 0; q < w / 32; ++q)
+            if (k * w + 32 * q < half)
+                o[q] = (spread32((uint32_t)(red >> (32 * q))) << pr) |
+                       (spread32((uint32_t)(blue >> (32 * q))) << (1 - pr));
     }
 }
 
-// packed bits -> planes, L % 64 == 0: one thread per plane word of both
-// colours (64 or 128 sites of a row).
+// packed bits -> planes, L % 64 == 0: one thread per plane word slot of both
+// colours; the bits of a last word past the row's valid sites stay zero.
 template <typename Word>
 __global__ void pack_spins_bits64_kernel(IoGeom g, const uint64_t* in) {
     constexpr int w = 8 * sizeof(Word);
-    const int64_t n = g.rows * g.W;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = t / g.W;
-        const int k = (int)(t - r * g.W);
-        const int pr = (int)((r % g.L + r / g.L) & 1);
+    const unsigned W = (unsigned)g.W, L = (unsigned)g.L, half = (unsigned)g.half;
+    const unsigned n = (unsigned)g.rows * W;
+    Word* P0 = (Word*)g.planes;
+    Word* P1 = (Word*)(g.planes + (size_t)4 * g.plane_bytes);
+    const unsigned stride = gridDim.x * blockDim.x;
+    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
+        const unsigned r = t / W, k = t - r * W;
+        const unsigned pr = (r % L + r / L) & 1u;
+        const uint64_t* ip = in + (size_t)r * (L / 64) + (size_t)k * (w / 32);
         Word red = 0, blue = 0;
 #pragma unroll
-        for (int q = 0; q < w / 32; ++q) {
-            const uint64_t v = in[(r * g.L + (int64_t)(k * w + 32 * q) * 2) / 64];
-            red |= (Word)compact32(v >> pr) << (32 * q);
-            blue |= (Word)compact32(v >> (1 - pr)) << (32 * q);
-        }
-        ((Word*)(g.planes + (size_t)0 * g.plane_bytes))[r * g.W + k] = red;
-        ((Word*)(g.planes + (size_t)4 * g.plane_bytes))[r * g.W + k] = blue;
+        for (int q = 0; q < w / 32; ++q)
+            if (k * w + 32 * q < half) {
+                const uint64_t v = ip[q];
+                red |= (Word)compact32(v >> pr) << (32 * q);
+                blue |= (Word)compact32(v >> (1 - pr)) << (32 * q);
+            }
+        P0[t] = red;
+        P1[t] = blue;
     }
 }
 
@@ -300,7 +307,7 @@ cudaError_t launch_pack_spins_checked(const isg_sim* h, const int8_t* in, unsign
 cudaError_t launch_unpack_spins_bits(const isg_sim* h, uint32_t* out, cudaStream_t s) {
     const IoGeom g = iogeom(h);
     if (g.L % 64 == 0) {
-        const unsigned grid = io_grid(g.rows * (g.L / 64), 256);
+        const unsigned grid = io_grid(g.rows * g.W, 256);
         if (h->wbits == 64) unpack_spins_bits64_kernel<uint64_t><<<grid, 256, 0, s>>>(g, (uint64_t*)out);
         else unpack_spins_bits64_kernel<uint32_t><<<grid, 256, 0, s>>>(g, (uint64_t*)out);
         return cudaGetLastError();

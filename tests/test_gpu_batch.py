@@ -264,3 +264,29 @@ def test_pass_engine_wait_gives_up_with_a_status(isg):
     Et, _ = b.tracked()
     assert np.array_equal(Em, Et)
     b.close()
+
+
+def test_member_packed_spin_io(isg):
+    """Batch members keep 64-bit words whatever L; where L / 2 is an odd
+    multiple of 32 (L = 64, 192) the last word of a row holds 32 valid sites.
+    Packed-bit spin I/O on such members against the int8 path: read after
+    sweeps, a round trip of a random configuration, tail bits left zero (the
+    energy bookkeeping and the trajectory afterwards stay exact)."""
+    L = [64, 192, 128]
+    b = isg.Batch(L, [11, 12, 13], [21, 22, 23, 24, 25, 26], [1 / 0.9] * 3, "mt19937")
+    b.run(3, group_sweeps=3)
+    for r in range(2 * len(L)):
+        m = b.member(r)
+        n = L[r // 2]
+        ref = m.read_spins()
+        np.testing.assert_array_equal(m.read_spins_packed(), np.packbits(ref == 1, bitorder="little"))
+        rng = np.random.default_rng(r)
+        s = np.where(rng.random(n ** 3) < 0.5, 1, -1).astype(np.int8)
+        m.write_spins_packed(np.packbits(s == 1, bitorder="little"))
+        np.testing.assert_array_equal(m.read_spins(), s)
+        assert m.tracked_energy() == m.energy()
+    b.run(2, group_sweeps=2)
+    E, _ = b.measure()
+    Et, _ = b.tracked()
+    assert np.array_equal(E, Et)
+    b.close()
