@@ -285,6 +285,9 @@ def test_member_packed_spin_io(isg):
         m.write_spins_packed(np.packbits(s == 1, bitorder="little"))
         np.testing.assert_array_equal(m.read_spins(), s)
         assert m.tracked_energy() == m.energy()
+        m.write_spins(-s)                                   # the int8 path on the same layout
+        np.testing.assert_array_equal(m.read_spins_packed(), np.packbits(-s == 1, bitorder="little"))
+        assert m.tracked_energy() == m.energy()
     b.run(2, group_sweeps=2)
     E, _ = b.measure()
     Et, _ = b.tracked()
