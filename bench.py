@@ -261,7 +261,7 @@ def batched_section(a, stream) -> dict:
     b = isg.Batch([x.L for x in samples], [x.seed_J for x in samples],
                   [v for x in samples for v in x.seed_spin], [1.0 / x.T for x in samples], "mt19937")
     attempts = b.info()["attempts_per_sweep"]
-    tuned = b.autotune(sweeps=8, stream=stream)       # untimed: candidates timed on a twin batch
+    tuned = b.autotune(sweeps=16, stream=stream)      # untimed: candidates timed on a twin batch
     group = 64
     b.run(group, group, stream)                      # warm-up (captures the graph)
     torch.cuda.synchronize()
@@ -278,9 +278,10 @@ def batched_section(a, stream) -> dict:
            "psflip": ms * 1e9 / (sweeps * attempts),
            "samples_sweeps_per_s": len(samples) * sweeps / (ms / 1e3),
            "autotune": {"config": list(tuned["config"]), "candidates": len(tuned["table"]),
-                        "psflip_by_config_8_sweeps": {"%d/%d/%d/%d" % tuple(c): round(p, 4) for c, p in tuned["table"]},
-                        "note": "config = CTA shape (0: 32x1, 1: 24x1, 2: 16x1, 3: 16x2 warps x CTAs per SM) / "
-                                "streams per bundle / resident generator state / words per lane"}}
+                        "psflip_by_config_16_sweeps": {"%d/%d/%d/%d" % tuple(c): round(p, 4) for c, p in tuned["table"]},
+                        "note": "config = engine (0: 32x1, 1: 24x1, 2: 16x1, 3: 16x2 warps x CTAs per SM, persistent "
+                                "bundles; 4: one launch per colour pass; 5: one launch per sweep group, per-lattice "
+                                "waits) / streams per bundle / resident generator state / words per lane"}}
     members = [b.member(r) for r in range(2 * len(samples))]
     for name, fn in (("plain_one_sample_per_launch_psflip", "sweep_plain"),
                      ("fast_one_sample_per_launch_psflip", "sweep")):
