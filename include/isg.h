@@ -144,7 +144,9 @@ int isg_read_spins_packed(const isg_sim *h, uint8_t *host_out, size_t nbytes, vo
  *   1. if in != NULL: overwrite the spins from packed bits (the format of
  *      isg_read_spins_packed, Sec. 4 bit map; every bit pattern is a valid
  *      configuration) and restart the energy bookkeeping (Eq. 1) from the new
- *      configuration, on the device;
+ *      configuration, on the device: with sweeps > 0 the first colour pass
+ *      counts the configuration's unsatisfied bonds before its flips (every
+ *      bond has one site of each colour), otherwise a separate popcount pass;
  *   2. `sweeps` sweeps (as isg_sweep);
  *   3. if out != NULL: the packed spins into out;
  *   4. if E_out != NULL: the tracked energy (int64, as isg_tracked_energy) into

@@ -159,6 +159,13 @@ __global__ void restart_on_device_kernel(long long* scal, long long threeN, long
     scal[0] = 2 * scal[1] - threeN - E0;
 }
 
+// The same restart folded into the first colour pass after new spins came in:
+// that pass counted the configuration's unsatisfied bonds U into scal[1] before
+// its flips and their dE into scal[0], so dE := dE + E(before the pass) - E0.
+__global__ void restart_after_pass_kernel(long long* scal, long long threeN, long long E0) {
+    scal[0] += 2 * scal[1] - threeN - E0;
+}
+
 // scal[4] = E0 + dE, the tracked energy, for an asynchronous read.
 __global__ void tracked_word_kernel(long long* scal, long long E0) { scal[4] = E0 + scal[0]; }
 
@@ -456,20 +463,37 @@ int isg_exchange_async(isg_sim* h, const uint8_t* in, uint8_t* out, size_t nbyte
         if (!h->stage) { set_error("isg_exchange_async: device allocation failed"); return ISG_ERR_NOMEM; }
     }
     cudaError_t e = cudaSuccess;
+    int64_t left = sweeps;
     if (in) {
         e = cudaMemcpyAsync(h->stage, in, need, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = launch_pack_spins_bits(h, h->stage, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(h->scal + 1, 0, sizeof(long long), s);
-        if (e == cudaSuccess) e = launch_energy(h, h->scal + 1, s);
-        if (e == cudaSuccess) {
-            restart_on_device_kernel<<<1, 1, 0, s>>>(h->scal, 3 * (long long)N, (long long)h->E0);
-            e = cudaGetLastError();
+        if (e == cudaSuccess && sweeps > 0) {
+            // the first red pass counts the new configuration's bonds before its
+            // flips, so no separate energy pass over the planes is needed
+            e = cudaMemsetAsync(h->scal, 0, 2 * sizeof(long long), s);
+            if (e == cudaSuccess) e = launch_flip_fast(h, 0, s, (unsigned long long*)(h->scal + 1));
+            if (e == cudaSuccess) {
+                restart_after_pass_kernel<<<1, 1, 0, s>>>(h->scal, 3 * (long long)N, (long long)h->E0);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = launch_flip_fast(h, 1, s);
+            if (e == cudaSuccess) {
+                h->sweeps += 1;
+                left -= 1;
+            }
+        } else if (e == cudaSuccess) {
+            e = cudaMemsetAsync(h->scal + 1, 0, sizeof(long long), s);
+            if (e == cudaSuccess) e = launch_energy(h, h->scal + 1, s);
+            if (e == cudaSuccess) {
+                restart_on_device_kernel<<<1, 1, 0, s>>>(h->scal, 3 * (long long)N, (long long)h->E0);
+                e = cudaGetLastError();
+            }
         }
         if (e != cudaSuccess) return cuda_fail(e, "isg_exchange_async: spins in");
     }
     h->last_stream = s;
-    if (sweeps > 0) {
-        const int rc = isg_sweep(h, sweeps, stream);
+    if (left > 0) {
+        const int rc = isg_sweep(h, left, stream);
         if (rc) return rc;
     }
     if (out) {

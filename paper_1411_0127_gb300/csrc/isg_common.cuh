@@ -319,7 +319,9 @@ cudaError_t launch_init_planes(isg_sim* h, cudaStream_t s);
 cudaError_t launch_init_rng(isg_sim* h, cudaStream_t s);
 FlipArgs make_flip_args(isg_sim* h, int colour);
 cudaError_t launch_flip_plain(isg_sim* h, int colour, cudaStream_t s);
-cudaError_t launch_flip_fast(isg_sim* h, int colour, cudaStream_t s);
+// usum (may be NULL): a device word that receives the pass's count of
+// unsatisfied bonds before its flips (U of Eq. 1, E = 2U - 3N)
+cudaError_t launch_flip_fast(isg_sim* h, int colour, cudaStream_t s, unsigned long long* usum = nullptr);
 cudaError_t launch_energy(const isg_sim* h, long long* out, cudaStream_t s);
 cudaError_t launch_overlap(const isg_sim* a, const isg_sim* b, long long* out, cudaStream_t s);
 cudaError_t launch_hash(const isg_sim* h, unsigned long long* out, cudaStream_t s);

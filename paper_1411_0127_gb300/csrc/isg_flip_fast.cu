@@ -50,9 +50,9 @@ struct Segments {
 
 // The throughput form keeps 7 (MT19937: shared memory) or 8 blocks of 4 warps
 // per SM; the latency form runs with few warps and may use more registers.
-template <typename Word, int KIND, bool TRIM>
+template <typename Word, int KIND, bool TRIM, bool USUM>
 __global__ void __launch_bounds__(kFastWarps * 32, TRIM ? (KIND == ISG_RNG_MT19937 ? 7 : 8) : 2)
-    flip_fast_kernel(FlipArgs a, StreamConst k, Tickets tk, Segments sg) {
+    flip_fast_kernel(FlipArgs a, StreamConst k, Tickets tk, Segments sg, unsigned long long* usum) {
     // Programmatic dependent launch: wait for the previous pass (its spins,
     // generator states and ticket count) before touching any of them.
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -63,6 +63,8 @@ __global__ void __launch_bounds__(kFastWarps * 32, TRIM ? (KIND == ISG_RNG_MT199
     uint32_t* cond = ring + kRing;
     const int64_t items = a.S * sg.nseg;
     int dEsum = 0;
+    int ulocal = 0;  // USUM: unsatisfied bonds counted before the pass's flips
+    int* up = USUM ? &ulocal : nullptr;
     // Items come from the ticket counter, except in the MINSTD latency form
     // (segmented launches), which takes them statically, item u by CTA u mod
     // grid, so that every SM gets work (L = 256 MINSTD 1.34 -> 1.25 ps, L = 32
@@ -94,7 +96,7 @@ __global__ void __launch_bounds__(kFastWarps * 32, TRIM ? (KIND == ISG_RNG_MT199
             if (rb < re) {
                 st.xA = minstd_mulmod(minstd_mulmod(x0, sg.jump[ks]), a.mt.pow[lane + 1]);
                 st.xB = minstd_mulmod(st.xA, k.a32);
-                stream_pass<Word, KIND, kFastSlack, TRIM>(a, a.c, rb, re, ring, cond, st, k, lane, dEsum);
+                stream_pass<Word, KIND, kFastSlack, TRIM>(a, a.c, rb, re, ring, cond, st, k, lane, dEsum, up);
             }
             if (ks == sg.nseg - 1 && lane == 0)
                 sg.rng_out[t] = minstd_mulmod(x0, t == a.S - 1 ? sg.jend_last : sg.jend);
@@ -102,7 +104,7 @@ __global__ void __launch_bounds__(kFastWarps * 32, TRIM ? (KIND == ISG_RNG_MT199
             const int64_t t = u;
             load_stream<KIND>(a, t, ring, st, k, lane);
             const int64_t rb = t * a.R, re = rb + a.R < a.rows ? rb + a.R : a.rows;
-            stream_pass<Word, KIND, kFastSlack, TRIM>(a, a.c, rb, re, ring, cond, st, k, lane, dEsum);
+            stream_pass<Word, KIND, kFastSlack, TRIM>(a, a.c, rb, re, ring, cond, st, k, lane, dEsum, up);
             store_stream<KIND>(a, t, ring, st, lane);
         }
     }
@@ -111,6 +113,10 @@ __global__ void __launch_bounds__(kFastWarps * 32, TRIM ? (KIND == ISG_RNG_MT199
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     for (int sh = 16; sh; sh >>= 1) dEsum += __shfl_xor_sync(kFull, dEsum, sh);
     if (lane == 0 && dEsum != 0) atomicAdd((unsigned long long*)a.dE, (unsigned long long)(long long)dEsum);
+    if (USUM) {
+        for (int sh = 16; sh; sh >>= 1) ulocal += __shfl_xor_sync(kFull, ulocal, sh);
+        if (lane == 0 && ulocal != 0) atomicAdd(usum, (unsigned long long)ulocal);
+    }
 }
 
 // Streams per SM from which the throughput form of the draw phase (TRIM) is used:
@@ -156,7 +162,7 @@ static Segments plan_segments(const isg_sim* h, int64_t resident_warps, bool lat
 }
 
 template <typename Word, int KIND, bool TRIM>
-static cudaError_t launch_fast_t(isg_sim* h, int colour, cudaStream_t s, int sms) {
+static cudaError_t launch_fast_t(isg_sim* h, int colour, cudaStream_t s, int sms, unsigned long long* usum) {
     const FlipArgs a = make_flip_args(h, colour);
     const StreamConst k = stream_const();
     Tickets tk;
@@ -165,7 +171,7 @@ static cudaError_t launch_fast_t(isg_sim* h, int colour, cudaStream_t s, int sms
     constexpr int kRing = KIND == ISG_RNG_MT19937 ? mt_window(kFastSlack) : 0;
     const size_t smem = (size_t)kFastWarps * (kRing + 2 * kCondWords) * sizeof(uint32_t);
     static std::atomic<int> occ_cache[kDeviceSlots];  // resident blocks per SM of this instantiation
-    const int occ = occupancy_cached(occ_cache, flip_fast_kernel<Word, KIND, TRIM>, kFastWarps * 32, smem);
+    const int occ = occupancy_cached(occ_cache, flip_fast_kernel<Word, KIND, TRIM, false>, kFastWarps * 32, smem);
     const Segments sg = plan_segments(h, (int64_t)sms * occ * kFastWarps, !TRIM);
     const int64_t items = h->S * sg.nseg;
     int64_t blocks = (int64_t)sms * occ;
@@ -186,7 +192,9 @@ static cudaError_t launch_fast_t(isg_sim* h, int colour, cudaStream_t s, int sms
     at[0].val.programmaticStreamSerializationAllowed = 1;
     lc.attrs = at;
     lc.numAttrs = (TRIM || sg.nseg > 1) ? 1 : 0;
-    cudaError_t e = cudaLaunchKernelEx(&lc, flip_fast_kernel<Word, KIND, TRIM>, a, k, tk, sg);
+    // with usum, the instantiation that also counts the pass's unsatisfied bonds
+    cudaError_t e = usum ? cudaLaunchKernelEx(&lc, flip_fast_kernel<Word, KIND, TRIM, true>, a, k, tk, sg, usum)
+                         : cudaLaunchKernelEx(&lc, flip_fast_kernel<Word, KIND, TRIM, false>, a, k, tk, sg, usum);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // with tickets, every warp takes one ticket past the last item before it stops
@@ -196,16 +204,16 @@ static cudaError_t launch_fast_t(isg_sim* h, int colour, cudaStream_t s, int sms
     return e;
 }
 
-cudaError_t launch_flip_fast(isg_sim* h, int colour, cudaStream_t s) {
+cudaError_t launch_flip_fast(isg_sim* h, int colour, cudaStream_t s, unsigned long long* usum) {
     const int sms = sm_count();
     const bool trim = h->S >= kTrimStreamsPerSM * sms;
     return with_kind(h->kind, [&](auto kind) {
         constexpr int K = decltype(kind)::value;
         if (h->wbits == 64)
-            return trim ? launch_fast_t<uint64_t, K, true>(h, colour, s, sms)
-                        : launch_fast_t<uint64_t, K, false>(h, colour, s, sms);
-        return trim ? launch_fast_t<uint32_t, K, true>(h, colour, s, sms)
-                    : launch_fast_t<uint32_t, K, false>(h, colour, s, sms);
+            return trim ? launch_fast_t<uint64_t, K, true>(h, colour, s, sms, usum)
+                        : launch_fast_t<uint64_t, K, false>(h, colour, s, sms, usum);
+        return trim ? launch_fast_t<uint32_t, K, true>(h, colour, s, sms, usum)
+                    : launch_fast_t<uint32_t, K, false>(h, colour, s, sms, usum);
     });
 }
 

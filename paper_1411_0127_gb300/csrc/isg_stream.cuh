@@ -243,7 +243,8 @@ __device__ __forceinline__ void word_load(const FlipArgs& a, int c, int r, int y
 
 template <typename Word>
 __device__ __forceinline__ void word_compute(const FlipArgs& a, int c, const WordIn<Word>& q, int k,
-                                             const uint32_t* cond, int off, int& dEsum, int hi_off = kCondWords) {
+                                             const uint32_t* cond, int off, int& dEsum, int hi_off = kCondWords,
+                                             int* usum = nullptr) {
     constexpr int w = 8 * sizeof(Word);
     const int W = a.W, nt = a.nt;
     Word* Sc = (Word*)(a.planes + (size_t)(4 * c) * (size_t)a.plane_bytes);
@@ -265,17 +266,24 @@ __device__ __forceinline__ void word_compute(const FlipArgs& a, int c, const Wor
     const Word lo = take_bits<Word>(cond, off);
     const Word hi = take_bits<Word>(cond + hi_off, off);
     Word f = Logic<Word>::flip(u0, u1, u2, lo | hi, hi, lo & hi);
-    if (k == W - 1 && nt < w) f &= (Word)((Word(1) << nt) - 1);
+    const Word valid = (k == W - 1 && nt < w) ? (Word)((Word(1) << nt) - 1) : ~Word(0);
+    f &= valid;
     Sc[q.o] = s ^ f;
     dEsum += Logic<Word>::dE(f, u0, u1, u2);
+    // the pass's unsatisfied bonds before any flip: every bond has one site of
+    // each colour, so their sum over one colour's sites is U of Eq. 1 (E = 2U - 3N)
+    if (usum)
+        *usum += Logic<Word>::popc(u0 & valid) + 2 * Logic<Word>::popc(u1 & valid) +
+                 4 * Logic<Word>::popc(u2 & valid);
 }
 
 template <typename Word>
 __device__ __forceinline__ void word_update(const FlipArgs& a, int c, int r, int y, int z, int k,
-                                            const uint32_t* cond, int off, int& dEsum, int hi_off = kCondWords) {
+                                            const uint32_t* cond, int off, int& dEsum, int hi_off = kCondWords,
+                                            int* usum = nullptr) {
     WordIn<Word> q;
     word_load<Word>(a, c, r, y, z, k, q);
-    word_compute<Word>(a, c, q, k, cond, off, dEsum, hi_off);
+    word_compute<Word>(a, c, q, k, cond, off, dEsum, hi_off, usum);
 }
 
 // Generator state of the stream a warp is working on.
@@ -426,7 +434,7 @@ __device__ __forceinline__ void clear_hi(uint32_t* hi, int n, int lane) {
 template <typename Word, int KIND, int SLACK, bool TRIM, int WPT = 1>
 __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t r_begin, int64_t r_end, uint32_t* B,
                                             uint32_t* cond, StreamRegs& st, const StreamConst& k, int lane,
-                                            int& dEsum) {
+                                            int& dEsum, int* usum = nullptr) {
     constexpr int w = 8 * sizeof(Word);
     constexpr bool kMT = KIND == ISG_RNG_MT19937;
     constexpr int kCond = WPT * kCondWords;
@@ -555,8 +563,8 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t r_
         __syncwarp();
         if constexpr (WPT == 1) {
             if (act) {
-                if (TRIM) word_update<Word>(a, c, r, y, z, lk, cond, loff, dEsum);
-                else word_compute<Word>(a, c, win, lk, cond, loff, dEsum);
+                if (TRIM) word_update<Word>(a, c, r, y, z, lk, cond, loff, dEsum, kCondWords, usum);
+                else word_compute<Word>(a, c, win, lk, cond, loff, dEsum, kCondWords, usum);
             }
         } else {
 #pragma unroll
@@ -565,7 +573,7 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t r_
                 if (wi < nrows * W) {
                     const int jq = wi / W, kq = wi - jq * W;
                     const int rq = (int)g0 + jq;
-                    word_update<Word>(a, c, rq, rq % L, rq / L, kq, cond, jq * half + kq * w, dEsum, kCond);
+                    word_update<Word>(a, c, rq, rq % L, rq / L, kq, cond, jq * half + kq * w, dEsum, kCond, usum);
                 }
             }
         }

@@ -363,6 +363,19 @@ def test_exchange_async(isg, L, kind):
     o.sweep(2)
     assert np.array_equal(unpack(b_out), o.spins())
     assert int(E[0]) == o.energy()
+    # a configuration in with no sweep: the bookkeeping restarts by a separate popcount pass
+    b_in[:] = np.packbits(-s == 1, bitorder="little")
+    g.exchange_async(b_in, b_out, 0, E, st)
+    st.synchronize()
+    o.set_spins((-s).astype(np.int8))
+    assert np.array_equal(unpack(b_out), o.spins())
+    assert int(E[0]) == o.energy() == g.energy() == g.tracked_energy()
+    # and with one sweep: the first colour pass counts the bonds before its flips
+    g.exchange_async(b_in, b_out, 1, E, st)
+    st.synchronize()
+    o.sweep(1)
+    assert np.array_equal(unpack(b_out), o.spins())
+    assert int(E[0]) == o.energy() == g.energy() == g.tracked_energy()
 
     def run(pipelined):
         hs = [isg.Sim(L, 5 + j, 6 + j, 1 / 0.8, kind) for j in range(3)]
