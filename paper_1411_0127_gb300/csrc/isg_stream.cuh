@@ -72,13 +72,15 @@ inline StreamConst stream_const() {
 // Shared-memory words of one warp's MT19937 window with `slack` free slots.
 constexpr int mt_window(int slack) { return kMtN + slack; }
 
-// MT19937 twist of one word: x_{k+624} from x_k, x_{k+1}, x_{k+397}.  The odd
-// test uses b - 2 (b >> 1) = b & 1.
+// MT19937 twist of one word: x_{k+624} from x_k, x_{k+1}, x_{k+397}.  y and
+// x_{k+1} share their low bit, so the odd test is y - 2 (y >> 1) = y & 1, one
+// multiply-add on the shift y >> 1 that the twist needs anyway (testing the
+// low bit of x_{k+1} by its own shift cost one more FMA-pipe instruction per
+// draw: L = 1024 MT19937 1.169 -> 1.101 ps per attempt without it).
 __device__ __forceinline__ uint32_t mt_twist(uint32_t a, uint32_t b, uint32_t m, const MtMul& k) {
     const uint32_t y = (a & 0x80000000u) | (b & 0x7FFFFFFFu);
     const uint32_t ys = __umulhi(y, k.hi31);
-    const uint32_t bh = __umulhi(b, k.hi31);
-    const uint32_t odd = b - 2u * bh;
+    const uint32_t odd = y - 2u * ys;
     return m ^ ys ^ (odd * 0x9908B0DFu);
 }
 
@@ -120,8 +122,11 @@ __device__ __forceinline__ void mt_make_room(uint32_t* B, int& iA, int need, int
 }
 
 // Four 32-draw blocks (128 draws) at once.  Block j reads x_{k+32j+l+397},
-// which was appended 227 - 32j - l >= 100 draws before this step, so every
-// read of the step can precede every write (one warp barrier between).
+// which was appended 227 - 32j - l >= 100 draws before this step; the step's
+// reads (indices up to k + 524) and writes (from k + 624) never meet, so the
+// one warp barrier after the writes, which orders them before the next step's
+// reads, is the only one (a second one between the reads and the writes cost
+// 0.7 % at L = 1024).
 template <int SLACK, bool ROOM = true>
 __device__ __forceinline__ void mt_quad(uint32_t* B, int& iA, uint32_t d[4], const MtMul& k, int lane) {
     if (ROOM) mt_make_room<SLACK>(B, iA, 128, lane);
@@ -133,7 +138,6 @@ __device__ __forceinline__ void mt_quad(uint32_t* B, int& iA, uint32_t d[4], con
         b[j] = B[i + 1];
         m[j] = B[i + kMtM];
     }
-    __syncwarp();
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const uint32_t v = mt_twist(a[j], b[j], m[j], k);
@@ -146,12 +150,15 @@ __device__ __forceinline__ void mt_quad(uint32_t* B, int& iA, uint32_t d[4], con
     for (int j = 0; j < 4; ++j) d[j] = mt_temper_mul(d[j], k);
 }
 
-// Seven 32-draw blocks (224 draws) at once, for warps too few to hide latency:
-// block j reads x_{k+32j+l+397} with 32j + l + 397 <= 620 < 624, i.e. words that
-// exist before the step, so the reads again all precede the writes.  227 draws is
-// the most one step of the recurrence allows.
+// The twist half of a seven-block step (224 draws) for warps too few to hide
+// latency: the raw words x_{k+624+32j+l} of blocks j = 0..6, appended to the
+// window and returned untempered in v.  Block j reads x_{k+32j+l+397} with
+// 32j + l + 397 <= 620 < 624, i.e. words that exist before the step, so no read
+// of the step touches a word the step writes and the step needs no barrier of
+// its own; the caller puts one warp barrier between consecutive steps.  227
+// draws is the most one step of the recurrence allows.
 template <int SLACK>
-__device__ __forceinline__ void mt_seven(uint32_t* B, int& iA, uint32_t d[7], const MtMul& k, int lane) {
+__device__ __forceinline__ void mt_seven_raw(uint32_t* B, int& iA, uint32_t v[7], const MtMul& k, int lane) {
     mt_make_room<SLACK>(B, iA, 224, lane);
     uint32_t a[7], b[7], m[7];
 #pragma unroll
@@ -161,26 +168,22 @@ __device__ __forceinline__ void mt_seven(uint32_t* B, int& iA, uint32_t d[7], co
         b[j] = B[i + 1];
         m[j] = B[i + kMtM];
     }
-    __syncwarp();
 #pragma unroll
     for (int j = 0; j < 7; ++j) {
-        const uint32_t v = mt_twist(a[j], b[j], m[j], k);
-        B[iA + 32 * j + lane + kMtN] = v;
-        d[j] = v;
+        v[j] = mt_twist(a[j], b[j], m[j], k);
+        B[iA + 32 * j + lane + kMtN] = v[j];
     }
-    __syncwarp();
     iA += 224;
-#pragma unroll
-    for (int j = 0; j < 7; ++j) d[j] = mt_temper_mul(d[j], k);
 }
 
-// One block of up to 32 draws (tail of a row group); lanes >= nvalid consume nothing.
+// One block of up to 32 draws (tail of a row group); lanes >= nvalid consume
+// nothing.  Reads reach k + 428 and writes start at k + 624: one barrier, after
+// the writes.
 template <int SLACK>
 __device__ __forceinline__ uint32_t mt_single(uint32_t* B, int& iA, int lane, int nvalid, const MtMul& k) {
     mt_make_room<SLACK>(B, iA, 32, lane);
     const int i = iA + lane;
     const uint32_t a = B[i], b = B[i + 1], m = B[i + kMtM];
-    __syncwarp();
     const uint32_t v = mt_twist(a, b, m, k);
     if (lane < nvalid) B[i + kMtN] = v;
     __syncwarp();
@@ -361,6 +364,28 @@ __device__ __forceinline__ void level_ballots(const uint32_t (&d)[N], const Cmp&
     }
 }
 
+// Tempering, level ballots and condition-stream words of a seven-block step
+// (raw words v, step q of the row group): lane j < 7 stores the ballots of
+// block j.
+__device__ __forceinline__ void seven_cond(const uint32_t (&v)[7], const Cmp& a, uint32_t* cond, int kCond, int q,
+                                           const MtMul& k, int lane) {
+    uint32_t d[7], lo[7], hi[7];
+#pragma unroll
+    for (int j = 0; j < 7; ++j) d[j] = mt_temper_mul(v[j], k);
+    level_ballots<7>(d, a, lo, hi);
+    uint32_t l = lo[0], h = hi[0];
+#pragma unroll
+    for (int j = 1; j < 7; ++j)
+        if (lane == j) {
+            l = lo[j];
+            h = hi[j];
+        }
+    if (lane < 7) {
+        cond[7 * q + lane] = l;
+        cond[kCond + 7 * q + lane] = h;
+    }
+}
+
 // The throughput form of the ballots of a quad of blocks.  A draw below cmp2 has
 // probability exp(-8 beta) (1.4e-4 at T = 0.9), so the warp first asks whether
 // any of its 128 draws is below cmp2.  If none is, none is below cmp3 either,
@@ -463,22 +488,23 @@ __device__ __forceinline__ void stream_pass(const FlipArgs& a, int c, int64_t r_
         // remaining blocks one by one
         int b = 0;  // 32-draw blocks of this group done so far
         if (kMT && !TRIM) {
+            // software-pipelined: the twist of step q + 1 is made beside the
+            // tempering and ballots of step q, two independent chains that one
+            // warp per scheduler can interleave
             const int nsev = D / 224;
-            for (int q = 0; q < nsev; ++q) {
-                uint32_t d[7], lo[7], hi[7];
-                mt_seven<SLACK>(B, st.iA, d, k.mul, lane);
-                level_ballots<7>(d, cm, lo, hi);
-                uint32_t l = lo[0], h = hi[0];
+            if (nsev > 0) {
+                uint32_t v[7];
+                mt_seven_raw<SLACK>(B, st.iA, v, k.mul, lane);
+                __syncwarp();
+                for (int q = 0; q + 1 < nsev; ++q) {
+                    uint32_t vn[7];
+                    mt_seven_raw<SLACK>(B, st.iA, vn, k.mul, lane);
+                    seven_cond(v, cm, cond, kCond, q, k.mul, lane);
+                    __syncwarp();
 #pragma unroll
-                for (int j = 1; j < 7; ++j)
-                    if (lane == j) {
-                        l = lo[j];
-                        h = hi[j];
-                    }
-                if (lane < 7) {
-                    cond[7 * q + lane] = l;
-                    cond[kCond + 7 * q + lane] = h;
+                    for (int j = 0; j < 7; ++j) v[j] = vn[j];
                 }
+                seven_cond(v, cm, cond, kCond, nsev - 1, k.mul, lane);
             }
             b = 7 * nsev;
         } else if (KIND == ISG_RNG_MINSTD && !TRIM) {
