@@ -97,8 +97,23 @@ int isg_info(const isg_sim *h, int *L, int *word_bits, int *words_per_row,
 
 /* Enqueue n full sweeps (red pass, then blue pass) on cuda_stream (async).
  * n >= 0.  The fused energy change of every accepted flip is accumulated on the
- * device (read with isg_tracked_energy).  Sec. 1 (colour order), Sec. 4 (rule). */
+ * device (read with isg_tracked_energy).  Sec. 1 (colour order), Sec. 4 (rule).
+ * Calls of at least 8 sweeps on MINSTD and MT19937 lattices with more RNG
+ * streams than such a launch has warps (see isg_sweep_info) run their passes
+ * in persistent launches of up to 64 sweeps: a
+ * stream starts a colour pass once the streams that hold its neighbouring rows
+ * have finished the previous pass.  Those waits are bounded; if one gives up, the remaining
+ * passes of the launch are skipped and the next isg_energy / isg_tracked_energy
+ * returns ISG_ERR_TIMEOUT (once).  The trajectory is the same in every form. */
 int isg_sweep(isg_sim *h, int64_t n, void *cuda_stream);
+
+/* How isg_sweep launches this handle's passes on the current device (host
+ * only): *passes_per_launch = 128 when calls of 8 or more sweeps run in
+ * persistent launches of up to 64 sweeps (a MINSTD or MT19937 lattice with at
+ * least as many RNG streams as the launch has warps, plus a margin: L >= ~640
+ * on a GB300), else 1 (one launch per colour pass, as for every call of fewer
+ * sweeps and every Parisi-Rapuano lattice). */
+int isg_sweep_info(const isg_sim *h, int *passes_per_launch);
 
 /* Same as isg_sweep but with the plain per-colour kernel: one stream per warp,
  * draws and bit logic in separate phases, no persistence.  Results are
@@ -405,6 +420,13 @@ int isg_stencil_decisions(const uint16_t *code, const uint32_t *draw, int64_t n,
 /* First n draws of stream t of the handle's generator, from its current
  * position, without advancing it (sync); host_out gets the 32-bit draws. */
 int isg_peek_draws(const isg_sim *h, int64_t t, int64_t n, uint32_t *host_out);
+
+/* Make the next multi-pass sweep launch of the handle (see isg_sweep) wait for
+ * a pass that never comes in its second pass, so that its bounded waits run out
+ * (about a second) and the error path can be tested: the launch skips its
+ * remaining passes and the next energy read returns ISG_ERR_TIMEOUT.
+ * ISG_ERR_STATE if the handle's sweeps do not run as multi-pass launches. */
+int isg_sweep_test_stall(isg_sim *h);
 
 /* Make one wait of the batch's launches wait for something that never comes,
  * so that its bounded wait runs out (about 4 s per launch) and the error path

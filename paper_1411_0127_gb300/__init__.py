@@ -38,6 +38,7 @@ SIGNATURES = {
     "isg_sweep": (_i32, [_vp, _i64, _vp]),
     "isg_sweep_plain": (_i32, [_vp, _i64, _vp]),
     "isg_sweeps_done": (_i32, [_vp, _vp]),
+    "isg_sweep_info": (_i32, [_vp, _vp]),
     "isg_energy": (_i32, [_vp, _vp, _vp]),
     "isg_tracked_energy": (_i32, [_vp, _vp]),
     "isg_overlap": (_i32, [_vp, _vp, _vp, _vp]),
@@ -54,6 +55,7 @@ SIGNATURES = {
     "isg_stencil_decisions": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp]),
     "isg_peek_draws": (_i32, [_vp, _i64, _i64, _vp]),
     "isg_batch_test_stall": (_i32, [_vp]),
+    "isg_sweep_test_stall": (_i32, [_vp]),
     "isg_energy_static_scratch": (_i32, [_vp, _vp, _vp]),
     "isg_batch_create": (_i32, [_i32, _vp, _vp, _vp, _vp, _i32, _PP]),
     "isg_batch_destroy": (None, [_vp]),
@@ -224,6 +226,13 @@ class Sim:
 
     def sweep_plain(self, n: int = 1, stream=None):
         _check(lib().isg_sweep_plain(self._h, int(n), _stream(stream)))
+
+    def passes_per_launch(self) -> int:
+        """128 if isg_sweep runs this lattice's passes in persistent launches of up
+        to 64 sweeps, 1 if it launches every colour pass on its own."""
+        v = ctypes.c_int()
+        _check(lib().isg_sweep_info(self._h, ctypes.byref(v)))
+        return v.value
 
     def sweeps_done(self) -> int:
         v = ctypes.c_int64()

@@ -106,13 +106,16 @@ static int alloc_sim(isg_sim* h) {
     h->rng_pos = (uint32_t*)dev_alloc(h, (size_t)h->S * 4);
     if (h->kind == ISG_RNG_MINSTD) h->rng_alt = (uint32_t*)dev_alloc(h, rng_words * 4);
     h->scal = (long long*)dev_alloc(h, 8 * sizeof(long long));
-    if (!h->planes || !h->rng || !h->rng_pos || !h->scal || (h->kind == ISG_RNG_MINSTD && !h->rng_alt)) {
+    if (!h->member) h->done = (unsigned long long*)dev_alloc(h, (size_t)h->S * sizeof(unsigned long long));
+    if (!h->planes || !h->rng || !h->rng_pos || !h->scal || (h->kind == ISG_RNG_MINSTD && !h->rng_alt) ||
+        (!h->member && !h->done)) {
         set_error("isg: device allocation failed (%zu bytes of planes)", pbytes);
         return ISG_ERR_NOMEM;
     }
     cudaError_t e = cudaMemset(h->planes, 0, pbytes);
     if (e == cudaSuccess) e = cudaMemset(h->scal, 0, 8 * sizeof(long long));
     if (e == cudaSuccess) e = cudaMemset(h->rng_pos, 0, (size_t)h->S * 4);
+    if (e == cudaSuccess && h->done) e = cudaMemset(h->done, 0, (size_t)h->S * sizeof(unsigned long long));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
     return ISG_OK;
 }
@@ -124,6 +127,7 @@ static void free_sim(isg_sim* h) {
     dev_free(h, h->rng_pos);
     dev_free(h, h->rng_alt);
     dev_free(h, h->scal);
+    dev_free(h, h->done);
     dev_free(h, h->stage);
     delete h;
 }
@@ -139,17 +143,28 @@ static isg_sim* new_sim() {
 }
 
 // Energy from scratch into *E, on stream s (sync).
+// ISG_ERR_TIMEOUT (once: the word is cleared) if the handle's error word scal[5]
+// is set: a bounded wait of a multi-pass sweep launch gave up, so passes were
+// skipped and the configuration is no longer on its trajectory.
+static int wait_error(const isg_sim* h, long long word, cudaStream_t s) {
+    if (word == 0) return ISG_OK;
+    cudaMemsetAsync(h->scal + 5, 0, sizeof(long long), s);
+    set_error("a bounded wait of a multi-pass sweep launch gave up: passes were skipped");
+    return ISG_ERR_TIMEOUT;
+}
+
 static int energy_sync(const isg_sim* h, int64_t* E, cudaStream_t s) {
     long long* acc = h->scal + 1;
     cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     e = launch_energy(h, acc, s);
     if (e != cudaSuccess) return cuda_fail(e, "energy kernel launch");
-    long long U = 0;
-    e = cudaMemcpyAsync(&U, acc, sizeof U, cudaMemcpyDeviceToHost, s);
+    long long w[5] = {0, 0, 0, 0, 0};  // scal[1..5]: U, ..., the error word
+    e = cudaMemcpyAsync(w, acc, sizeof w, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "energy");
-    *E = 2 * (int64_t)U - 3 * (int64_t)h->L * h->L * h->L;
+    if (const int rc = wait_error(h, w[4], s)) return rc;
+    *E = 2 * (int64_t)w[0] - 3 * (int64_t)h->L * h->L * h->L;
     return ISG_OK;
 }
 
@@ -222,7 +237,8 @@ size_t sim_device_bytes(int L, int rng_kind, bool member) {
     partition(L, &R, &S);
     const int64_t plane = (rows * W * (wbits / 8) + 255) / 256 * 256;
     const int64_t rng = S * rng_state_words(rng_kind) * 4 * (rng_kind == ISG_RNG_MINSTD ? 2 : 1);
-    return (size_t)(8 * plane + rng + S * 4 + 8 * (int64_t)sizeof(long long));
+    const int64_t done = member ? 0 : S * (int64_t)sizeof(unsigned long long);
+    return (size_t)(8 * plane + rng + S * 4 + 8 * (int64_t)sizeof(long long) + done);
 }
 
 }  // namespace isg
@@ -287,13 +303,35 @@ int isg_sweep_plain(isg_sim* h, int64_t n, void* stream) {
 int isg_sweep(isg_sim* h, int64_t n, void* stream) {
     if (!h || n < 0) { set_error("isg_sweep: bad handle or n"); return ISG_ERR_ARG; }
     cudaStream_t s = (cudaStream_t)stream;
-    for (int64_t k = 0; k < n; ++k) {
-        cudaError_t e = launch_flip_fast(h, 0, s);
-        if (e == cudaSuccess) e = launch_flip_fast(h, 1, s);
-        if (e != cudaSuccess) return cuda_fail(e, "flip kernel launch");
+    if (sweeps_in_one_launch(h, n)) {
+        // enough streams and sweeps: all passes in persistent launches of up to 64 sweeps
+        const cudaError_t e = launch_sweeps(h, n, s);
+        if (e != cudaSuccess) return cuda_fail(e, "sweep kernel launch");
+    } else {
+        for (int64_t k = 0; k < n; ++k) {
+            cudaError_t e = launch_flip_fast(h, 0, s);
+            if (e == cudaSuccess) e = launch_flip_fast(h, 1, s);
+            if (e != cudaSuccess) return cuda_fail(e, "flip kernel launch");
+        }
     }
     h->sweeps += n;
     h->last_stream = s;
+    return ISG_OK;
+}
+
+int isg_sweep_info(const isg_sim* h, int* passes_per_launch) {
+    if (!h || !passes_per_launch) { set_error("isg_sweep_info: NULL argument"); return ISG_ERR_ARG; }
+    *passes_per_launch = sweeps_in_one_launch(h, 64) ? 128 : 1;
+    return ISG_OK;
+}
+
+int isg_sweep_test_stall(isg_sim* h) {
+    if (!h) { set_error("isg_sweep_test_stall: NULL handle"); return ISG_ERR_ARG; }
+    if (!sweeps_in_one_launch(h, 64)) {
+        set_error("isg_sweep_test_stall: this handle's sweeps do not run as multi-pass launches");
+        return ISG_ERR_STATE;
+    }
+    h->stall_next = true;
     return ISG_OK;
 }
 
@@ -310,11 +348,12 @@ int isg_energy(isg_sim* h, int64_t* E, void* stream) {
 
 int isg_tracked_energy(isg_sim* h, int64_t* E) {
     if (!h || !E) { set_error("isg_tracked_energy: NULL argument"); return ISG_ERR_ARG; }
-    long long d = 0;
-    cudaError_t e = cudaMemcpyAsync(&d, h->scal, sizeof d, cudaMemcpyDeviceToHost, h->last_stream);
+    long long w[6] = {0, 0, 0, 0, 0, 0};  // scal[0..5]: dE, ..., the error word
+    cudaError_t e = cudaMemcpyAsync(w, h->scal, sizeof w, cudaMemcpyDeviceToHost, h->last_stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->last_stream);
     if (e != cudaSuccess) return cuda_fail(e, "isg_tracked_energy");
-    *E = h->E0 + (int64_t)d;
+    if (const int rc = wait_error(h, w[5], h->last_stream)) return rc;
+    *E = h->E0 + (int64_t)w[0];
     return ISG_OK;
 }
 

@@ -275,7 +275,12 @@ struct isg_sim {
     uint32_t* rng_pos = nullptr;        // MT: S ring positions
     uint32_t* rng_alt = nullptr;        // MINSTD: the other state buffer of segmented passes (see isg_flip_fast.cu)
     long long* scal = nullptr;          // [0] tracked dE, [1] scratch sum, [2] hash, [3] stream tickets,
-                                        // [4] energy word of isg_exchange_async
+                                        // [4] energy word of isg_exchange_async, [5] error word (a bounded
+                                        // wait of a multi-pass launch gave up)
+    unsigned long long* done = nullptr; // per stream: colour passes completed by multi-pass launches (not
+                                        // for batch members)
+    unsigned long long passes = 0;      // colour passes of all multi-pass launches so far
+    bool stall_next = false;            // testing: the next multi-pass launch's pass-1 waits never end
     uint32_t* stage = nullptr;          // packed-spin staging buffer of isg_exchange_async (made on first use)
     unsigned long long tickets = 0;     // value of the stream-ticket counter before the next launch
     int64_t E0 = 0;                     // energy when tracking (re)started
@@ -334,6 +339,10 @@ cudaError_t launch_flip_plain(isg_sim* h, int colour, cudaStream_t s);
 // usum (may be NULL): a device word that receives the pass's count of
 // unsatisfied bonds before its flips (U of Eq. 1, E = 2U - 3N)
 cudaError_t launch_flip_fast(isg_sim* h, int colour, cudaStream_t s, unsigned long long* usum = nullptr);
+// n full sweeps as persistent launches of up to 64 sweeps each (isg_flip_fast.cu):
+// only where sweeps_in_one_launch(h, n) holds (enough streams, n >= 8)
+bool sweeps_in_one_launch(const isg_sim* h, int64_t n);
+cudaError_t launch_sweeps(isg_sim* h, int64_t n, cudaStream_t s);
 cudaError_t launch_energy(const isg_sim* h, long long* out, cudaStream_t s);
 cudaError_t launch_overlap(const isg_sim* a, const isg_sim* b, long long* out, cudaStream_t s);
 cudaError_t launch_hash(const isg_sim* h, unsigned long long* out, cudaStream_t s);

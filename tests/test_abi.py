@@ -75,6 +75,8 @@ def test_other_host_side_checks(isg):
     assert lib.isg_write_spins_packed(None, None, 0, None) == isg.ISG_ERR_ARG
     assert lib.isg_info(None, None, None, None, None, None) == isg.ISG_ERR_ARG
     assert lib.isg_sweep(None, 1, None) == isg.ISG_ERR_ARG
+    assert lib.isg_sweep_test_stall(None) == isg.ISG_ERR_ARG
+    assert lib.isg_sweep_info(None, None) == isg.ISG_ERR_ARG
     # one allocator function without the other
     f = isg._ALLOC_T(lambda n, c: None)
     assert lib.isg_set_allocator(ctypes.cast(f, ctypes.c_void_p), None, None) == isg.ISG_ERR_ARG

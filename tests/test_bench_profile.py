@@ -1,5 +1,5 @@
 """bench.py reads the committed ncu summary of the flip kernel (DRAM bytes per
-launch, issue utilisation) only while the summary was taken on the current
+colour pass, issue utilisation) only while the summary was taken on the current
 kernel source: a changed kernel gives null, never a stale figure."""
 import os
 import shutil
@@ -25,7 +25,7 @@ def bench_copy(tmp_path, monkeypatch):
 def test_committed_summary_matches_the_current_source(bench_copy):
     bench, _ = bench_copy
     t = bench.traffic_from_profile("mt19937")
-    assert t is not None and 5e8 < t < 1e9           # about 654 MB per launch at L = 1024
+    assert t is not None and 5e8 < t < 1e9           # about 650 MB per colour pass at L = 1024
     iss = bench.issue_from_profile("mt19937")
     assert iss is not None and 0 < iss["issue_active"] <= 1
     assert iss["warp_instructions_per_32_attempts"] > 17   # at least the algorithmic ops

@@ -270,6 +270,71 @@ def test_throughput_form_lattices(isg, L, kind):
     assert np.array_equal(g.read_spins(), o.spins())
 
 
+@pytest.mark.parametrize("kind", ["minstd", "mt19937"])
+@pytest.mark.parametrize("L", [640, 704])
+def test_multi_pass_launches(isg, L, kind):
+    """MT19937 and MINSTD lattices with more streams than a launch has warps
+    (L = 640: 7877 streams, 64-bit words; L = 704: 8125 streams, 32-bit words)
+    run all passes
+    of an isg_sweep call in persistent launches of up to 64 sweeps, each
+    stream's pass starting once its neighbouring streams have finished the
+    previous one (L = 432 and 512 keep one launch per pass; calls of fewer
+    than 8 sweeps too).  65 sweeps in one call (two launches: 64 + 1), the same
+    65 as one call per sweep, and the plain per-colour kernel reach the same
+    configuration; ten sweeps in calls of 1 + 9 against the oracle, all spins;
+    an exchange of ten sweeps (one of single passes, then nine in a multi-pass
+    launch) continues the same trajectory."""
+    a = isg.Sim(L, L + 3, L + 4, 1 / 0.9, kind)
+    b = isg.Sim(L, L + 3, L + 4, 1 / 0.9, kind)
+    c = isg.Sim(L, L + 3, L + 4, 1 / 0.9, kind)
+    assert a.passes_per_launch() == 128
+    assert isg.Sim(512, 1, 2, 1.0, kind).passes_per_launch() == 1
+    assert isg.Sim(L, 1, 2, 1.0, "parisi_rapuano").passes_per_launch() == 1
+    a.sweep(65)
+    for _ in range(65):
+        b.sweep(1)
+    c.sweep_plain(65)
+    assert a.hash() == b.hash() == c.hash()
+    assert a.tracked_energy() == b.tracked_energy() == c.tracked_energy() == a.energy()
+    for h in (a, b, c):
+        h.close()
+    g, o = pair(isg, L, kind, 1 / 1.1, seed_J=L + 5, seed_spin=L + 6)
+    g.sweep(1)
+    g.sweep(9)
+    o.sweep(10, threads=16)
+    assert g.tracked_energy() == o.tracked_energy()
+    assert np.array_equal(g.read_spins(), o.spins())
+    bits = g.read_spins_packed()
+    E = np.zeros(1, dtype=np.int64)
+    g.exchange_async(bits, None, 10, E)     # one sweep of single passes, then a multi-pass launch
+    o.sweep(10, threads=16)
+    import torch
+    torch.cuda.synchronize()
+    assert int(E[0]) == g.tracked_energy() == o.tracked_energy() == g.energy()
+    assert g.hash() == o.hash()
+
+
+def test_multi_pass_wait_gives_up_with_a_status(isg):
+    """A multi-pass launch whose second pass waits for a pass that never comes
+    (the isg_sweep_test_stall hook): its bounded waits run out, the rest of the
+    launch is skipped, the next energy read reports ISG_ERR_TIMEOUT once, and the
+    context stays usable."""
+    g = isg.Sim(640, 1, 2, 1 / 0.9, "minstd")
+    assert isg.lib().isg_sweep_test_stall(g.handle) == isg.ISG_OK
+    g.sweep(8)
+    with pytest.raises(isg.IsgError) as ei:
+        g.tracked_energy()
+    assert ei.value.code == isg.ISG_ERR_TIMEOUT
+    g.tracked_energy()                       # reported once
+    g.close()
+    small = isg.Sim(64, 1, 2, 1 / 0.9, "minstd")
+    assert isg.lib().isg_sweep_test_stall(small.handle) == isg.ISG_ERR_STATE
+    h, o = pair(isg, 640, "mt19937", 1 / 0.9)
+    h.sweep(8)
+    o.sweep(8, threads=16)
+    assert h.tracked_energy() == o.tracked_energy() == h.energy()
+
+
 @pytest.mark.parametrize("L", [32, 50, 96, 130])
 def test_segmented_minstd_streams(isg, L):
     """MINSTD lattices with few streams run every stream as several row-group
