@@ -267,9 +267,11 @@ __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned l
 }
 
 // Whether item (pass p, rows [rb, re)) may start: false if the error word is set
-// or a wait gave up (which sets it).  The same answer in every lane.
-__device__ __forceinline__ bool pass_ready(const FlipArgs& a, const SweepPlan& sp, int64_t p, int64_t rb, int64_t re,
-                                           int lane) {
+// or a wait gave up (which sets it).  The same answer in every lane.  Not
+// inlined, so that its registers do not weigh on the draw loop's (with 32-bit
+// item indices: MINSTD 0.5525 -> 0.5266 ps at L = 1024, MT19937 unchanged).
+__device__ __noinline__ bool pass_ready(const FlipArgs& a, const SweepPlan& sp, int64_t p, int64_t rb, int64_t re,
+                                        int lane) {
     if (*(volatile const unsigned long long*)sp.err != 0ull) return false;
     if (p == 0) return true;  // the previous pass belongs to an earlier, completed launch
     const unsigned long long target = sp.base + (unsigned long long)p + (p == 1 ? sp.stall : 0ull);
@@ -313,17 +315,19 @@ __global__ void __launch_bounds__(kFastWarps * 32, KIND == ISG_RNG_MT19937 ? 7 :
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint32_t* ring = smem + wid * (kRing + 2 * kCondWords);
     uint32_t* cond = ring + kRing;
-    const int64_t S = a.S, items = sp.npass * S;
+    // 32-bit item indices: items <= 128 passes x 8192 streams, rows <= 2048^2
+    const int S = (int)a.S, items = (int)(sp.npass * a.S), R = (int)a.R, rows = (int)a.rows;
+    const int shift = (int)sp.shift;
     int dEsum = 0;
     for (;;) {
         unsigned long long v = 0;
         if (lane == 0) v = atomicAdd(tk.counter, 1ull);
         v = __shfl_sync(kFull, v, 0);
-        const int64_t u = (int64_t)(v - tk.base);
+        const int u = (int)(v - tk.base);  // at most items + the launch's warps
         if (u >= items) break;
-        const int64_t p = u / S;
-        const int64_t t = (u - p * S + (p * sp.shift) % S) % S;
-        const int64_t rb = t * a.R, re = rb + a.R < a.rows ? rb + a.R : a.rows;
+        const int p = u / S;
+        const int t = (u - p * S + (p * shift) % S) % S;
+        const int rb = t * R, re = rb + R < rows ? rb + R : rows;
         if (!pass_ready(a, sp, p, rb, re, lane)) continue;
         StreamRegs st;
         load_stream<KIND>(a, t, ring, st, k, lane);
