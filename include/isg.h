@@ -100,11 +100,13 @@ int isg_info(const isg_sim *h, int *L, int *word_bits, int *words_per_row,
  * device (read with isg_tracked_energy).  Sec. 1 (colour order), Sec. 4 (rule).
  * Calls of at least 8 sweeps on MINSTD and MT19937 lattices with more RNG
  * streams than such a launch has warps (see isg_sweep_info) run their passes
- * in persistent launches of up to 64 sweeps: a
- * stream starts a colour pass once the streams that hold its neighbouring rows
- * have finished the previous pass.  Those waits are bounded; if one gives up, the remaining
- * passes of the launch are skipped and the next isg_energy / isg_tracked_energy
- * returns ISG_ERR_TIMEOUT (once).  The trajectory is the same in every form. */
+ * in persistent launches of up to 64 sweeps: a stream starts a colour pass
+ * once the streams that hold its neighbouring rows have finished the previous
+ * pass.  Those waits are bounded.  If one gives up, the remaining passes of the
+ * launch are skipped, so are those of later multi-pass launches of the handle
+ * until the error has been read, and the next isg_energy / isg_tracked_energy
+ * returns ISG_ERR_TIMEOUT (once: reading it clears it); the configuration is
+ * then off its trajectory.  Every form gives the same trajectory. */
 int isg_sweep(isg_sim *h, int64_t n, void *cuda_stream);
 
 /* How isg_sweep launches this handle's passes on the current device (host
