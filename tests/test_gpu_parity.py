@@ -314,6 +314,24 @@ def test_multi_pass_launches(isg, L, kind):
     assert g.hash() == o.hash()
 
 
+def test_multi_pass_launches_maximum_size(isg):
+    """L = 2048, the largest lattice (8192 streams of 512 rows: a stream's z
+    neighbours are 4 streams away): 8 MT19937 sweeps in one multi-pass launch
+    equal 8 calls of one sweep (one launch per colour pass), and the tracked
+    energy equals the energy from scratch."""
+    a = isg.Sim(2048, 1, 2, 1 / 0.9, "mt19937")
+    assert a.passes_per_launch() == 128
+    a.sweep(8)
+    ha, Ea = a.hash(), a.tracked_energy()
+    assert Ea == a.energy()
+    a.close()
+    b = isg.Sim(2048, 1, 2, 1 / 0.9, "mt19937")
+    for _ in range(8):
+        b.sweep(1)
+    assert b.hash() == ha and b.tracked_energy() == Ea
+    b.close()
+
+
 def test_multi_pass_wait_gives_up_with_a_status(isg):
     """A multi-pass launch whose second pass waits for a pass that never comes
     (the isg_sweep_test_stall hook): its bounded waits run out, the rest of the
