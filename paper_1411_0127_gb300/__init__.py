@@ -222,6 +222,9 @@ class Sim:
                 "rows_per_stream": R.value}
 
     def sweep(self, n: int = 1, stream=None):
+        """Enqueue n sweeps (isg_sweep).  Calls of 8 or more sweeps on large MINSTD
+        and MT19937 lattices run as persistent multi-pass launches (see
+        passes_per_launch); the trajectory is the same either way."""
         _check(lib().isg_sweep(self._h, int(n), _stream(stream)))
 
     def sweep_plain(self, n: int = 1, stream=None):

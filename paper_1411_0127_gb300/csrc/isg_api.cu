@@ -148,7 +148,8 @@ static isg_sim* new_sim() {
 // skipped and the configuration is no longer on its trajectory.
 static int wait_error(const isg_sim* h, long long word, cudaStream_t s) {
     if (word == 0) return ISG_OK;
-    cudaMemsetAsync(h->scal + 5, 0, sizeof(long long), s);
+    const cudaError_t e = cudaMemsetAsync(h->scal + 5, 0, sizeof(long long), s);
+    if (e != cudaSuccess) return cuda_fail(e, "clearing the error word");
     set_error("a bounded wait of a multi-pass sweep launch gave up: passes were skipped");
     return ISG_ERR_TIMEOUT;
 }
